@@ -1,0 +1,315 @@
+"""FP64 CPU oracle of the QTAM analysis/synthesis pair (arXiv 2603.29785).
+
+TEST INFRASTRUCTURE ONLY.  This module is the slow, plain reference that the
+CUDA library is checked against.  Only ``tests/``, ``__graft_entry__.smoke()``
+and the CPU-baseline leg of ``bench.py`` may import it; the product path never
+does.  It shares no code with the library: geometry, windows, the frame
+operator and both transforms are written out again here from the paper, in
+float64, with numpy's FFT as the only library step (the FFT is itself pinned
+against a naive O(N^2) DFT by the tests).
+
+What is computed, in the paper's notation
+-----------------------------------------
+x       real segment of N samples at rate fs, duration T = N / fs (the paper's N_t)
+X[f]    one-sided DFT, f = 0 .. N/2                      (App. C, DFT definition)
+f_k     centre frequencies, log grid per plane             (App. A, frequency grid)
+k_c     centre bin round(f_k T)                            (Eq. support: k_c = f N_t)
+h       window half-width (the paper's Delta k_f)          (Eq. support; App. A clamp)
+W_k[f]  c_k (1 - ((f - k_c)/h)^2)^2 on |f - k_c| <= h      (Eq. gwpy_window_formula)
+M       envelope length (the paper's N_out)                (Sec. III, demodulation)
+Y_k[n]  sqrt(M/N) * IDFT_M of the band shifted to baseband (Sec. III; App. C,
+        "QTAM demodulation" normalisation)
+P[f]    sum_k W_k[f]^2, the diagonal frame operator        (App. C)
+x_hat   irfft( sum_k T~_k W_k / P )                        (Eq. qtam_canonical_inverse)
+
+Readings where the paper is silent or garbled (each is a plan option or a
+documented choice; the same list is kept in the design notes):
+  C1  log grid with both endpoints: f_k = fmin (fmax/fmin)^(k/(K-1)).
+  C2  h_ideal = floor(f_k T q_width / Q), q_width = sqrt(11) (rms half-width of
+      the bisquare's square is h/sqrt(11), so Q = f / sigma_f).
+  C3  Delta f_max = largest gap between consecutive centres; h_max =
+      floor(ceil(T Delta f_max) / 2)  (L_max = 2 h_max + 1, App. A clamp);
+      h = max(1, min(h_ideal, h_max)).  A manual clamp in Hz replaces Delta f_max.
+  C4  c_k = (sum_d W'(d)^2)^(-1/2) over the untruncated window ("L2", default);
+      "paper" = 1 / sum_d W'(d)^2 (Eq. gwpy_window_and_normalization read
+      literally); "none" = 1.
+  C5  M = smallest 2^a 3^b 5^c >= max_k L_k (lossless iff M >= L); N_in = N.
+  C6  windows are truncated to 0 <= f <= N/2 (no Hermitian folding).
+  C7  k_c rounds half away from zero.
+  C8  the inverse divides by P only on F_tau = {f : P[f] > 0, P[f] >= tau max P}
+      and sets X_hat = 0 elsewhere: the round trip is the orthogonal projection
+      of x onto F_tau.
+  C9  a plane mask selects the planes whose rows are synthesised and whose
+      windows enter P.
+
+Parity of every function here is pinned by the ``-m "not gpu"`` oracle tests.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+NORMS = ("l2", "paper", "none")
+
+
+# ----------------------------------------------------------------------------
+# geometry (App. A: frequency grid, window length, clamp)
+# ----------------------------------------------------------------------------
+def smooth_length(n: int) -> int:
+    """Smallest integer >= n whose only prime factors are 2, 3 and 5 (reading C5)."""
+    m = max(1, int(n))
+    while True:
+        r = m
+        for p in (2, 3, 5):
+            while r % p == 0:
+                r //= p
+        if r == 1:
+            return m
+        m += 1
+
+
+def log_grid(fmin: float, fmax: float, K: int) -> np.ndarray:
+    """Log-spaced centre frequencies, both endpoints included (App. A grid, reading C1)."""
+    if K == 1:
+        return np.array([float(fmin)])
+    k = np.arange(K, dtype=np.float64)
+    return fmin * (fmax / fmin) ** (k / (K - 1))
+
+
+def round_half_away(v: float) -> int:
+    """k_c = f N_t is not an integer (Eq. support); round half away from zero (C7)."""
+    return int(math.floor(abs(v) + 0.5)) * (1 if v >= 0 else -1)
+
+
+@dataclass
+class Geometry:
+    fs: float
+    N: int
+    qs: tuple
+    fmin: float
+    fmax: float
+    K: int
+    norm: str
+    q_width: float
+    h_max: int              # clamp half-width (App. A), or a huge value when unclamped
+    M: int                  # envelope length N_out
+    f: np.ndarray           # [P, K] centre frequencies
+    kc: np.ndarray          # [P, K] centre bins
+    h: np.ndarray           # [P, K] half-widths
+    c: np.ndarray           # [P, K] window normalisation c_k
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def P(self) -> int:
+        return len(self.qs)
+
+    @property
+    def T(self) -> float:
+        return self.N / self.fs
+
+    @property
+    def Nr(self) -> int:
+        return self.N // 2 + 1
+
+    @property
+    def L(self) -> np.ndarray:
+        return 2 * self.h + 1
+
+
+def bisquare_profile(d: np.ndarray, h: int) -> np.ndarray:
+    """Unnormalised bisquare W'(d) = (1 - (d/h)^2)^2 for |d| <= h, else 0.
+
+    Eq. gwpy_window_formula.  (1 - (d/h)^2) is formed as (h-|d|)(h+|d|)/h^2 with
+    the product taken exactly in integers, so values near the window edge carry
+    no cancellation error.
+    """
+    d = np.asarray(d, dtype=np.int64)
+    a = np.abs(d)
+    num = (h - a) * (h + a)                       # exact integer
+    u = num.astype(np.float64) / float(h * h)
+    return np.where(a <= h, u * u, 0.0)
+
+
+def window_norm(h: int, norm: str) -> float:
+    """c_k of Eq. gwpy_window_and_normalization under reading C4."""
+    d = np.arange(-h, h + 1)
+    s2 = float(np.sum(bisquare_profile(d, h) ** 2))
+    if norm == "l2":
+        return 1.0 / math.sqrt(s2)
+    if norm == "paper":
+        return 1.0 / s2
+    if norm == "none":
+        return 1.0
+    raise ValueError(norm)
+
+
+def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
+             max_window_hz=0.0, n_out=0) -> Geometry:
+    """Plan the filter bank: grid, centre bins, half-widths, c_k and M.
+
+    App. A (grid f_k, L_k^ideal proportional to f_k N_t / Q, automatic clamp
+    L_max = 2 floor(ceil(N_t Delta f_max)/2) + 1, L_k = min(L_k^ideal, L_max))
+    and Sec. IV's minimal output length, under readings C1-C5.
+    """
+    N = int(N)
+    if N <= 0 or N % 2:
+        raise ValueError("N must be a positive even integer")
+    T = N / fs
+    grid = log_grid(fmin, fmax, K)
+    if max_window_hz > 0:
+        df_max = float(max_window_hz)
+    elif K >= 2:
+        df_max = float(np.max(np.diff(grid)))
+    else:
+        df_max = math.inf
+    if math.isinf(df_max):
+        h_max = 1 << 62
+    else:
+        h_max = int(math.ceil(T * df_max)) // 2
+    P = len(qs)
+    f = np.zeros((P, K))
+    kc = np.zeros((P, K), dtype=np.int64)
+    h = np.zeros((P, K), dtype=np.int64)
+    c = np.zeros((P, K))
+    for p, Q in enumerate(qs):
+        for k in range(K):
+            f[p, k] = grid[k]
+            kc[p, k] = round_half_away(grid[k] * T)
+            h_ideal = int(math.floor(grid[k] * T * q_width / Q))
+            h[p, k] = max(1, min(h_ideal, h_max))
+            c[p, k] = window_norm(int(h[p, k]), norm)
+    Lmax = int(np.max(2 * h + 1))
+    if n_out:
+        if n_out < Lmax:
+            raise ValueError("n_out shorter than the largest window: aliasing")
+        M = int(n_out)
+    else:
+        M = smooth_length(Lmax)
+    return Geometry(fs=float(fs), N=N, qs=tuple(float(q) for q in qs), fmin=float(fmin),
+                    fmax=float(fmax), K=int(K), norm=norm, q_width=float(q_width),
+                    h_max=int(h_max), M=M, f=f, kc=kc, h=h, c=c)
+
+
+def window(g: Geometry, p: int, k: int) -> np.ndarray:
+    """Dense W_k[f], f = 0..N/2, truncated to the one-sided band (reading C6)."""
+    fbin = np.arange(g.Nr)
+    return g.c[p, k] * bisquare_profile(fbin - g.kc[p, k], int(g.h[p, k]))
+
+
+def frame_operator(g: Geometry, planes=None) -> np.ndarray:
+    """P[f] = sum_k |W_k[f]|^2 over the selected planes (App. C, frame operator)."""
+    planes = range(g.P) if planes is None else planes
+    Pf = np.zeros(g.Nr)
+    for p in planes:
+        for k in range(g.K):
+            Pf += window(g, p, k) ** 2
+    return Pf
+
+
+def kept_bins(Pf: np.ndarray, tau: float) -> np.ndarray:
+    """F_tau = {f : P[f] > 0 and P[f] >= tau max P} (reading C8)."""
+    return (Pf > 0) & (Pf >= tau * np.max(Pf))
+
+
+# ----------------------------------------------------------------------------
+# transforms
+# ----------------------------------------------------------------------------
+def spectrum(x: np.ndarray) -> np.ndarray:
+    """X[f] = sum_n x[n] exp(-2 pi i f n / N), f = 0..N/2 (App. C, DFT)."""
+    return np.fft.rfft(np.asarray(x, dtype=np.float64))
+
+
+def band(g: Geometry, p: int, k: int):
+    """Offsets d in [-h, h] whose bins k_c + d lie in 0..N/2, and those bins."""
+    hk = int(g.h[p, k])
+    d = np.arange(-hk, hk + 1)
+    fb = g.kc[p, k] + d
+    ok = (fb >= 0) & (fb <= g.N // 2)
+    return d[ok], fb[ok]
+
+
+def forward_row(g: Geometry, X: np.ndarray, p: int, k: int) -> np.ndarray:
+    """Envelope Y_k[n], n = 0..M-1, of one row (Sec. III demodulation; App. A).
+
+    1. filter:   S'_k[d] = W_k[k_c + d] X[k_c + d]     (element-wise product)
+    2. shift:    roll by -k_c so the band sits at baseband, Z[d mod M] = S'_k[d]
+                 (crop to the band, zero-pad symmetrically to M)
+    3. IFFT of length M and renormalise by sqrt(N_out / N_in) = sqrt(M/N):
+                 Y_k[n] = sqrt(M/N) * (1/M) sum_j Z[j] exp(+2 pi i j n / M)
+    """
+    d, fb = band(g, p, k)
+    Z = np.zeros(g.M, dtype=np.complex128)
+    w = g.c[p, k] * bisquare_profile(d, int(g.h[p, k]))
+    Z[d % g.M] = w * X[fb]
+    return np.fft.ifft(Z) * math.sqrt(g.M / g.N)
+
+
+def forward(g: Geometry, x: np.ndarray) -> np.ndarray:
+    """QTAM analysis of one segment: Y[p, k, n] complex128 of shape [P, K, M]."""
+    X = spectrum(x)
+    Y = np.zeros((g.P, g.K, g.M), dtype=np.complex128)
+    for p in range(g.P):
+        for k in range(g.K):
+            Y[p, k] = forward_row(g, X, p, k)
+    return Y
+
+
+def accumulate(g: Geometry, Y: np.ndarray, planes=None) -> np.ndarray:
+    """A[f] = sum_k W_k^*[f] T~_k[f]: the numerator of Eq. qtam_canonical_inverse.
+
+    Each row's tile spectrum is recovered from the envelope by an FFT of length
+    M, re-scaled by sqrt(N_in/N_out) = sqrt(N/M) and shifted back from baseband
+    to its carrier k_c (App. C, synthesis step), then weighted by the window.
+    """
+    planes = range(g.P) if planes is None else planes
+    A = np.zeros(g.Nr, dtype=np.complex128)
+    for p in planes:
+        for k in range(g.K):
+            S = np.fft.fft(Y[p, k]) * math.sqrt(g.N / g.M)
+            d, fb = band(g, p, k)
+            w = g.c[p, k] * bisquare_profile(d, int(g.h[p, k]))
+            A[fb] += w * S[d % g.M]
+    return A
+
+
+def real_ifft(Xh: np.ndarray, N: int) -> np.ndarray:
+    """Inverse of the one-sided DFT for a real signal; the imaginary parts of
+    the DC and Nyquist bins are dropped (the real signal's spectrum is
+    Hermitian there)."""
+    Xh = np.array(Xh, dtype=np.complex128)
+    Xh[0] = Xh[0].real
+    Xh[N // 2] = Xh[N // 2].real
+    return np.fft.irfft(Xh, n=N)
+
+
+def inverse(g: Geometry, Y: np.ndarray, planes=None, tau: float = 0.0) -> np.ndarray:
+    """Canonical dual-frame synthesis (Eq. qtam_canonical_inverse; App. C):
+    x_hat = F^-1{ A[f] / P[f] } on F_tau, 0 elsewhere (reading C8)."""
+    A = accumulate(g, Y, planes)
+    Pf = frame_operator(g, planes)
+    keep = kept_bins(Pf, tau)
+    Xh = np.zeros(g.Nr, dtype=np.complex128)
+    Xh[keep] = A[keep] / Pf[keep]
+    return real_ifft(Xh, g.N)
+
+
+def projection(g: Geometry, x: np.ndarray, planes=None, tau: float = 0.0) -> np.ndarray:
+    """x_proj = irfft(X 1[F_tau]): what an exact round trip returns (App. C
+    exact reconstruction where P > 0; reading C8 elsewhere)."""
+    X = spectrum(x)
+    keep = kept_bins(frame_operator(g, planes), tau)
+    return real_ifft(np.where(keep, X, 0.0), g.N)
+
+
+def kappa(g: Geometry, planes=None, tau: float = 0.0) -> float:
+    """Worst amplification of the dual frame on F_tau: max_f (max_k W_k[f]) / P[f]."""
+    planes = range(g.P) if planes is None else planes
+    Pf = frame_operator(g, planes)
+    Wmax = np.zeros(g.Nr)
+    for p in planes:
+        for k in range(g.K):
+            Wmax = np.maximum(Wmax, window(g, p, k))
+    keep = kept_bins(Pf, tau)
+    return float(np.max(Wmax[keep] / Pf[keep]))

@@ -1,0 +1,90 @@
+"""Plant plausible mistakes in the oracle (on the CPU) and check that the pins
+catch every one of them: a wrong sign, a dropped scale, an off-by-one shift,
+a wrong window exponent or normalisation, a wrong synthesis scale."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qtam_oracle as O
+from tests import test_oracle_pins as pins
+
+PIN_TESTS = [
+    lambda gd: pins.test_dense_tile_relation_bruteforce_time_domain(),
+    lambda gd: pins.test_round_trip_fp64_is_projection(),
+    lambda gd: pins.test_parseval_per_row_and_frame_energy(),
+    lambda gd: pins.test_adjoint_dot_product(),
+    lambda gd: pins.test_shift_invariance_one_decimation_step(),
+    lambda gd: pins.test_tone_peaks_on_its_row(),
+    lambda gd: pins.test_window_norms(),
+    lambda gd: pins.test_bisquare_shape_and_moments(),
+    lambda gd: pins.test_geometry_hand_derivations(gd),
+    lambda gd: pins.test_grid_and_widths_follow_formulas(),
+]
+
+
+def _fwd_wrong_sign(g, X, p, k):
+    d, fb = O.band(g, p, k)
+    Z = np.zeros(g.M, dtype=np.complex128)
+    Z[d % g.M] = g.c[p, k] * O.bisquare_profile(d, int(g.h[p, k])) * X[fb]
+    return np.fft.fft(Z) / g.M * math.sqrt(g.M / g.N)
+
+
+def _fwd_no_renorm(g, X, p, k):
+    d, fb = O.band(g, p, k)
+    Z = np.zeros(g.M, dtype=np.complex128)
+    Z[d % g.M] = g.c[p, k] * O.bisquare_profile(d, int(g.h[p, k])) * X[fb]
+    return np.fft.ifft(Z)
+
+
+def _fwd_shift_off_by_one(g, X, p, k):
+    d, fb = O.band(g, p, k)
+    Z = np.zeros(g.M, dtype=np.complex128)
+    Z[(d + 1) % g.M] = g.c[p, k] * O.bisquare_profile(d, int(g.h[p, k])) * X[fb]
+    return np.fft.ifft(Z) * math.sqrt(g.M / g.N)
+
+
+_orig_profile = O.bisquare_profile
+_orig_norm = O.window_norm
+_orig_acc = O.accumulate
+
+
+def _profile_linear(d, h):
+    return np.sqrt(_orig_profile(d, h))
+
+
+def _norm_sum_not_sqrt(h, norm):
+    c = _orig_norm(h, norm)
+    return c * c if norm == "l2" else c
+
+
+def _acc_wrong_scale(g, Y, planes=None):
+    return _orig_acc(g, Y, planes) * math.sqrt(g.M / g.N) / math.sqrt(g.N / g.M)
+
+
+def _acc_conj(g, Y, planes=None):
+    return _orig_acc(g, np.conj(Y), planes)
+
+
+MUTANTS = {
+    "ifft sign": ("forward_row", _fwd_wrong_sign),
+    "dropped sqrt(M/N)": ("forward_row", _fwd_no_renorm),
+    "baseband shift off by one": ("forward_row", _fwd_shift_off_by_one),
+    "window exponent 1": ("bisquare_profile", _profile_linear),
+    "c_k squared": ("window_norm", _norm_sum_not_sqrt),
+    "synthesis scale sqrt(M/N)": ("accumulate", _acc_wrong_scale),
+    "synthesis of conj(Y)": ("accumulate", _acc_conj),
+}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, monkeypatch, golden_dir):
+    attr, fn = MUTANTS[name]
+    monkeypatch.setattr(O, attr, fn)
+    caught = []
+    for t in PIN_TESTS:
+        try:
+            t(golden_dir)
+        except (AssertionError, ValueError, IndexError):
+            caught.append(t)
+    assert caught, f"no pin caught the mutant '{name}'"
