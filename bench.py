@@ -1,0 +1,325 @@
+"""Benchmark: QTAM forward + inverse throughput on GB300.
+
+Workload (one step = one pass of the whole path over one batch): 64 segments
+of 64 s at 4096 Hz (N = 262144) of coloured-then-whitened Gaussian noise with
+a Newtonian chirp (SNR 20), Q-planes {4, 8, 16, 32, 64} x 128 log rows from
+20 to 2048 Hz, envelopes M = 4800, FP32.  A step runs the long FFT, the
+envelope kernel, the accumulation kernel and the synthesis (1/P + inverse
+long FFT) through the library's C ABI.
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU
+oracle on the host instead, on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "QTAM fwd+inv Msamples/s and HBM-roofline % at FP32 vs FP64-oracle error; p99 latency"
+UNIT = "Msamples/s"
+WORKLOAD = dict(fs=4096.0, N=262144, qs=(4.0, 8.0, 16.0, 32.0, 64.0), fmin=20.0, fmax=2048.0, K=128)
+WORKLOAD_NAME = "64 s @ 4096 Hz segments, Q {4,8,16,32,64} x 128 log rows 20-2048 Hz, M=4800, FP32"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--batch", type=int, default=64, help="segments per GPU per step")
+    ap.add_argument("--impl", default="qtam", choices=["qtam", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-sample-segments", type=int, default=4)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+# ---------------------------------------------------------------------------- inputs
+def make_inputs(seeds):
+    from paper_2603_29785_gb300 import synth
+    return np.stack([synth.coloured_chirp_segment(int(s), n=WORKLOAD["N"], fs=WORKLOAD["fs"]) for s in seeds])
+
+
+# ---------------------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- reference arm
+def run_reference(args, rank):
+    """Time the FP64 CPU oracle (as it stands) on a bounded sample of the workload."""
+    if rank != 0:
+        return
+    from oracle import qtam_oracle as O
+    g = O.geometry(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"])
+    tau = 1e-6
+    x = make_inputs([0])[0].astype(np.float64)
+    for _ in range(max(0, min(args.warmup, 1))):
+        O.inverse(g, O.forward(g, x), tau=tau)
+    times = []
+    for s in range(args.steps):
+        t0 = time.perf_counter()
+        O.inverse(g, O.forward(g, x), tau=tau)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * WORKLOAD["N"] / total / 1e6
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "segments_per_step": 1, "N": WORKLOAD["N"], "M": g.M},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": "1 segment of the workload per step (forward + inverse, numpy FP64, one thread)"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------- GPU arm
+def cpu_baseline_leg(p, x_host, xh_gpu, y_gpu, nseg):
+    """Oracle on a bounded sample (nseg segments): timing + GPU-vs-oracle error."""
+    from oracle import qtam_oracle as O
+    g = O.geometry(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"])
+    tau = p.info["p_floor_rel"]
+    t0 = time.perf_counter()
+    errs_f, errs_rt = [], []
+    outs = []
+    for b in range(nseg):
+        xb = x_host[b].astype(np.float64)
+        Y = O.forward(g, xb)
+        xr = O.inverse(g, Y, tau=tau)
+        outs.append((Y, xr))
+    dt = time.perf_counter() - t0
+    for b, (Y, xr) in enumerate(outs):
+        errs_f.append(float(np.linalg.norm(y_gpu[b] - Y) / np.linalg.norm(Y)))
+        xp = xr  # oracle inverse of its own forward = projection onto F_tau
+        errs_rt.append(float(np.linalg.norm(xh_gpu[b] - xp) / np.linalg.norm(xp)))
+    return ({"value": nseg * WORKLOAD["N"] / dt / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+             "sample": f"{nseg} segments of the workload, forward + inverse, numpy FP64, one thread"},
+            {"forward_rel_err_max": max(errs_f), "roundtrip_rel_err_max": max(errs_rt),
+             "segments_checked": nseg, "tolerance": {"forward": 1e-6, "roundtrip": 1e-5}})
+
+
+def run_gpu(args, rank, world, local):
+    import torch
+    from paper_2603_29785_gb300 import qtam
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B = args.batch
+    seeds = [rank * B + i for i in range(B)]
+    x_host = make_inputs(seeds)
+    p = qtam.Plan(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"],
+                  device=local)
+    N, Nr, M, P, K = p.N, p.Nr, p.M, p.P, p.K
+    dev = f"cuda:{local}"
+    x = torch.from_numpy(x_host).to(dev)
+    X = torch.empty((B, Nr), dtype=torch.complex64, device=dev)
+    A = torch.empty((B, Nr), dtype=torch.complex64, device=dev)
+    y = p.envelope_tensor(B)
+    xh = torch.empty((B, N), dtype=torch.float32, device=dev)
+    ws, wsb = p.workspace(B)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)   # > 129 MB L2
+    st = torch.cuda.current_stream()
+    h = p.handle
+
+    def step():
+        qtam.qtam_stage_spectrum(h, x, B, X, ws, wsb, st)
+        ev[1].record(st)
+        qtam.qtam_stage_envelopes(h, X, B, y, st)
+        ev[2].record(st)
+        qtam.qtam_stage_accumulate(h, y, B, 0, A, st)
+        ev[3].record(st)
+        qtam.qtam_stage_synthesize(h, A, B, 0, xh, ws, wsb, st)
+
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    for _ in range(args.warmup):
+        flush.zero_()
+        ev[0].record(st)
+        step()
+        ev[4].record(st)
+    torch.cuda.synchronize()
+    stage_ms = np.zeros(4)
+    total_ms = 0.0
+    clocks = ClockSampler(local)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for _ in range(args.steps):
+        flush.zero_()
+        ev[0].record(st)
+        step()
+        ev[4].record(st)
+        ev[4].synchronize()
+        t = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
+        stage_ms += t
+        total_ms += ev[0].elapsed_time(ev[4])
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    clk = clocks.stop()
+    ms_per_step = total_ms / args.steps
+    if dist is not None:
+        tt = torch.tensor([ms_per_step], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms_per_step = float(tt.item())
+    samples_per_step = world * B * N
+    value = samples_per_step / (ms_per_step * 1e-3) / 1e6
+
+    # ---- end to end through the C ABI with host buffers (pinned) ----
+    x_pin = torch.from_numpy(x_host).pin_memory()
+    xh_pin = torch.empty((B, N), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        qtam.qtam_roundtrip_host(h, x_pin, B, 0, xh_pin, x, y, xh, ws, wsb, st)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_steps = max(3, args.steps // 2)
+    for _ in range(e2e_steps):
+        qtam.qtam_roundtrip_host(h, x_pin, B, 0, xh_pin, x, y, xh, ws, wsb, st)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    if dist is not None:
+        tt = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = float(tt.item())
+    e2e = {"value": samples_per_step / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": B * N * 4,
+           "d2h_bytes_per_step": B * N * 4, "ms_per_step": e2e_s * 1e3}
+
+    # ---- roofline of the dominant kernel (envelope kernel: writes B*P*K*M complex64) ----
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    env_bytes = B * P * K * M * 8
+    x_bytes = B * N * 4
+    stage_bytes = [x_bytes, env_bytes, env_bytes, x_bytes]       # algorithmic HBM bytes per stage launch
+    stage_names = ["spectrum (long R2C FFT)", "envelopes (k_rows_forward)", "accumulate (k_rows_inverse)",
+                   "synthesize (1/P + long C2R FFT)"]
+    stage_avg_ms = stage_ms / args.steps
+    kernels = {}
+    for nm, b, t in zip(stage_names, stage_bytes, stage_avg_ms):
+        kernels[nm] = {"ms": round(float(t), 4), "alg_bytes": int(b), "GB_s": round(b / (t * 1e-3) / 1e9, 1)}
+    dom = int(np.argmax(stage_avg_ms[1:3])) + 1
+    achieved = stage_bytes[dom] / (stage_avg_ms[dom] * 1e-3) / 1e9
+    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
+    traffic = None
+    try:
+        tr = json.load(open(traffic_path))
+        traffic = tr.get(["", "k_rows_forward", "k_rows_inverse"][dom], {}).get("bytes_per_launch_full")
+    except (OSError, ValueError):
+        pass
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved / hbm_peak, 4), "traffic": traffic, "kernel": stage_names[dom],
+                "peak_source": peak_src}
+    fwdinv_bytes = 2 * (env_bytes + x_bytes)
+    path_frac = fwdinv_bytes / (ms_per_step * 1e-3) / 1e9 / hbm_peak
+
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(ms_per_step, 4), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "segments_per_gpu": B, "N": N, "M": M, "planes": P,
+                   "rows_per_plane": K, "parallelism": f"replicas x{world}",
+                   "l2": "flushed between steps (256 MB write outside the timed events)"},
+        "roofline": roofline,
+        "path_hbm_frac": round(path_frac, 4),
+        "stages": kernels,
+        "e2e": e2e,
+        "gpu_launches": 7 * args.steps,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        nseg = max(1, min(args.cpu_sample_segments, B))
+        torch.cuda.synchronize()
+        yv = y[:nseg].cpu().numpy().astype(np.complex128)
+        xv = xh[:nseg].cpu().numpy().astype(np.float64)
+        cb, acc = cpu_baseline_leg(p, x_host, xv, yv, nseg)
+        line["cpu_baseline"] = cb
+        line["accuracy"] = acc
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    run_gpu(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,184 @@
+/*
+ * qtam.h -- C ABI of the GB300-native QTAM library (invertible Q-transform,
+ * "Q-Transform Amplitude Modulation", arXiv 2603.29785).
+ *
+ * The library computes, on one GPU, the QTAM analysis (forward) and
+ * canonical dual-frame synthesis (inverse) of real segments:
+ *
+ *   forward  (Sec. III; App. A):  X = rfft_N(x);  for every Q-plane p and
+ *            log-spaced row k, S'_k[d] = W_k[k_c+d] X[k_c+d] on |d| <= h_k,
+ *            shifted to baseband, zero-padded to M and inverse-transformed:
+ *            Y_k[n] = (M N)^(-1/2) sum_j S'_k[j] exp(+2 pi i j n / M).
+ *   inverse  (Eq. qtam_canonical_inverse; App. C):  per row the FFT of Y_k,
+ *            re-scaled by sqrt(N/M) and shifted back to k_c, weighted by
+ *            W_k and summed into A[f]; X_hat = A / P on the kept bins
+ *            F_tau = {P > 0, P >= tau max P}, 0 elsewhere; x_hat = irfft_N.
+ *
+ *   W_k[f] = c_k (1 - ((f - k_c)/h_k)^2)^2 on |f - k_c| <= h_k, 0 <= f <= N/2
+ *            (Eq. gwpy_window_formula, Eq. support)
+ *   P[f]   = sum over the selected planes and rows of W_k[f]^2 (App. C frame
+ *            operator), computed in FP64 on the host when the plan is made.
+ *
+ * Conventions for every entry point:
+ *  - Pointers named x, y, workspace are DEVICE pointers on the plan's device,
+ *    owned by the caller; the library never frees them.  *_host pointers are
+ *    host memory (pinned for asynchronous copies).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Every launch is asynchronous on that stream; nothing
+ *    synchronises unless stated.
+ *  - Argument and size errors are returned synchronously before any launch.
+ *    Launch errors are returned as QTAM_ERR_CUDA; asynchronous faults surface
+ *    at the caller's next synchronisation.  qtam_last_error() gives a message
+ *    for the calling thread's last failure.  No exception crosses the ABI.
+ *  - Plans are immutable after creation except for a cache of per-mask
+ *    normalisers (guarded by a mutex) and may be used from several streams at
+ *    once, each call with its own workspace.
+ *
+ * Layouts (row-major, no padding):
+ *   x      [batch][N]          real, float (compute F32) or double (F64)
+ *   y      [batch][P][K][M]    complex, interleaved (re, im): float2,
+ *                              bf16x2 or half2 (envelope dtype), or double2
+ *   column n of a row is time n*T/M from the segment start (circular).
+ */
+#ifndef QTAM_H
+#define QTAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define QTAM_API __attribute__((visibility("default")))
+#else
+#define QTAM_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct qtam_plan_s* qtam_plan_t;
+
+typedef enum {
+  QTAM_OK = 0,
+  QTAM_ERR_INVALID_ARG = 1,      /* null pointer, negative size, bad enum, bad mask */
+  QTAM_ERR_UNSUPPORTED_SIZE = 2, /* N or M outside what the kernels handle */
+  QTAM_ERR_ALIASING = 3,         /* requested n_out shorter than the largest window */
+  QTAM_ERR_NO_COVERAGE = 4,      /* the selected planes cover no frequency bin */
+  QTAM_ERR_OUT_OF_MEMORY = 5,    /* plan tables could not be allocated */
+  QTAM_ERR_CUDA = 6,             /* a CUDA runtime call or launch failed */
+  QTAM_ERR_TIMEOUT = 7,          /* a bounded device-side wait expired */
+  QTAM_ERR_NO_DEVICE = 8,        /* the plan was made host-only (device = -1) */
+  QTAM_ERR_WORKSPACE = 9         /* workspace smaller than qtam_workspace_size() */
+} qtam_status;
+
+enum { QTAM_WIN_BISQUARE = 0 };
+/* window normalisation c_k: L2 = (sum W'^2)^(-1/2) (unit-energy window);
+ * PAPER = 1 / sum W'^2 (Eq. gwpy_window_and_normalization read literally);
+ * NONE = 1. */
+enum { QTAM_NORM_L2 = 0, QTAM_NORM_PAPER = 1, QTAM_NORM_NONE = 2 };
+enum { QTAM_DTYPE_F32 = 0, QTAM_DTYPE_F64 = 1, QTAM_DTYPE_BF16 = 2, QTAM_DTYPE_F16 = 3 };
+
+typedef struct {
+  double sample_rate;     /* f_s in Hz, > 0 */
+  int64_t length;         /* N samples per segment; even, N/2 a multiple of 16 with factors 2,3,5 */
+  const double* q;        /* n_q quality factors, one Q-plane each (copied) */
+  int32_t n_q;            /* 1 .. 64 */
+  double f_min, f_max;    /* log grid f_k = f_min (f_max/f_min)^(k/(K-1)), endpoints included */
+  int32_t rows_per_plane; /* K >= 1 */
+  int32_t window;         /* QTAM_WIN_BISQUARE */
+  int32_t norm;           /* QTAM_NORM_* */
+  double q_width;         /* half-width h = floor(f T q_width / Q); <= 0 selects sqrt(11) */
+  double max_window_hz;   /* 0: automatic clamp from the largest centre gap (App. A); > 0: manual */
+  int32_t n_out;          /* M; 0: smallest 2^a 3^b 5^c >= the largest window */
+  int32_t compute_dtype;  /* QTAM_DTYPE_F32 or QTAM_DTYPE_F64 */
+  int32_t envelope_dtype; /* F32/BF16/F16 with F32 compute; F64 with F64 compute */
+  double p_floor_rel;     /* tau; < 0 selects the default (1e-6 for F32, 0 for F64) */
+} qtam_plan_desc;
+
+typedef struct {
+  int64_t length;                 /* N */
+  int64_t n_bins;                 /* N/2 + 1 */
+  int32_t n_planes;               /* P */
+  int32_t rows_per_plane;         /* K */
+  int32_t n_out;                  /* M */
+  int32_t h_max;                  /* clamp half-width (huge when unclamped) */
+  int32_t max_window;             /* max_k L_k = 2 h_k + 1 */
+  int32_t compute_dtype;
+  int32_t envelope_dtype;
+  int32_t fft_n1, fft_n2;         /* four-step split of the N/2-point long FFT */
+  int64_t envelope_bytes_per_segment; /* P*K*M * bytes per complex */
+  int64_t band_bins;              /* sum over rows of the in-band window bins */
+  double p_floor_rel;             /* tau in use */
+  double kappa;                   /* max over kept bins of max_k W_k / P (all planes) */
+  int64_t kept_bins;              /* |F_tau| for all planes */
+  int64_t device_bytes;           /* bytes of resident plan tables on the device */
+} qtam_plan_info_t;
+
+/* Fill *d with defaults: bisquare, L2 norm, q_width sqrt(11), automatic clamp
+ * and n_out, F32 compute and envelopes, default floor.  Sizes stay zero. */
+QTAM_API void qtam_plan_desc_init(qtam_plan_desc* d);
+
+/* Build a plan (App. A geometry, FP64 frame operator, twiddle tables) and
+ * upload its tables to `device`.  device = -1 makes a host-only plan whose
+ * geometry can be queried but which cannot run transforms.  The plan owns its
+ * device tables until qtam_destroy.  Synchronous. */
+QTAM_API qtam_status qtam_plan(const qtam_plan_desc* desc, int device, qtam_plan_t* out);
+
+QTAM_API qtam_status qtam_plan_info(qtam_plan_t plan, qtam_plan_info_t* out);
+
+/* Per-row geometry, row r = p*K + k, each array caller-owned with P*K
+ * entries (any may be NULL): centre frequency f_k (Hz), centre bin k_c,
+ * half-width h_k and normalisation c_k. */
+QTAM_API qtam_status qtam_plan_rows(qtam_plan_t plan, double* f, int64_t* kc, int32_t* h, double* c);
+
+/* Frame operator P[f], f = 0..N/2, of the planes in plane_mask (bit p =
+ * plane p; 0 = all planes), FP64, into the caller's host array of N/2+1. */
+QTAM_API qtam_status qtam_frame_operator(qtam_plan_t plan, uint64_t plane_mask, double* p_out);
+
+/* Bytes of device workspace one qtam_forward/qtam_inverse call on `batch`
+ * segments needs (the long-FFT buffers and the spectrum accumulator). */
+QTAM_API qtam_status qtam_workspace_size(qtam_plan_t plan, int64_t batch, size_t* bytes);
+
+/* QTAM analysis of `batch` segments: x [batch][N] -> y [batch][P][K][M].
+ * batch = 0 is a no-op.  workspace_bytes must be >= qtam_workspace_size. */
+QTAM_API qtam_status qtam_forward(qtam_plan_t plan, const void* x, int64_t batch, void* y,
+                         void* workspace, size_t workspace_bytes, void* stream);
+
+/* QTAM synthesis by the canonical dual frame of the planes in plane_mask
+ * (0 = all): y [batch][P][K][M] -> x [batch][N].  Rows of unselected planes
+ * are not read.  Any y is accepted (e.g. masked or row-zeroed envelopes). */
+QTAM_API qtam_status qtam_inverse(qtam_plan_t plan, const void* y, int64_t batch, uint64_t plane_mask,
+                         void* x, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Stage entry points of the same path, for stage-level checks and custom
+ * pipelines.  spectrum: x -> X [batch][N/2+1] complex (step a1).
+ * envelopes: X -> y (steps a2-a4).  accumulate: y -> A [batch][N/2+1]
+ * complex, zeroed first (steps a5-a6).  synthesize: A -> x with the 1/P of
+ * plane_mask and the inverse long FFT (step a7).  workspace as above. */
+QTAM_API qtam_status qtam_stage_spectrum(qtam_plan_t plan, const void* x, int64_t batch, void* X,
+                                void* workspace, size_t workspace_bytes, void* stream);
+QTAM_API qtam_status qtam_stage_envelopes(qtam_plan_t plan, const void* X, int64_t batch, void* y, void* stream);
+QTAM_API qtam_status qtam_stage_accumulate(qtam_plan_t plan, const void* y, int64_t batch, uint64_t plane_mask,
+                                  void* A, void* stream);
+QTAM_API qtam_status qtam_stage_synthesize(qtam_plan_t plan, const void* A, int64_t batch, uint64_t plane_mask,
+                                  void* x, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Forward then inverse from HOST buffers: copies x_host into x_dev, runs
+ * qtam_forward into y_dev and qtam_inverse into xhat_dev, and copies xhat_dev
+ * back into xhat_host, all on `stream`; synchronises the stream before
+ * returning.  All device buffers are caller-owned ([batch][N], [batch][P][K][M],
+ * [batch][N]). */
+QTAM_API qtam_status qtam_roundtrip_host(qtam_plan_t plan, const void* x_host, int64_t batch, uint64_t plane_mask,
+                                void* xhat_host, void* x_dev, void* y_dev, void* xhat_dev,
+                                void* workspace, size_t workspace_bytes, void* stream);
+
+/* Release the plan's device tables and the plan.  NULL is a no-op. */
+QTAM_API qtam_status qtam_destroy(qtam_plan_t plan);
+
+QTAM_API const char* qtam_status_string(qtam_status s);
+QTAM_API const char* qtam_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QTAM_H */

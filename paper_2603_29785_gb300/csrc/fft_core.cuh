@@ -1,0 +1,289 @@
+// Device FFT engine shared by the long-FFT and row kernels.
+//
+// A transform of length m = r_0 r_1 ... r_{S-1} (radices 2, 3, 4, 5, 8, 16)
+// runs as S Stockham autosort stages inside one thread block.  Stage s with
+// span Ns = r_0...r_{s-1} and radix R takes, for each butterfly j < m/R,
+//   a_i = in[j + i m/R]                               (i < R)
+//   a_i *= w_m^(+-i (j mod Ns) m/(Ns R))               (twiddle table)
+//   b   = DFT_R(a)
+//   out[(j/Ns) Ns R + (j mod Ns) + i Ns] = b_i
+// so the first stage reads its inputs with unit stride across threads and the
+// last stage writes its outputs with unit stride: the first stage reads global
+// memory through a Load functor and the last writes global memory through a
+// Store functor; only the stages in between exchange through shared memory.
+// `nb` transforms (a power of two) can run side by side, interleaved as
+// element (b, i) -> smem[i*nb + b].
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <utility>
+
+namespace qtam {
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename T> struct cvec;
+template <> struct cvec<float> { using type = float2; };
+template <> struct cvec<double> { using type = double2; };
+template <typename T> using cplx = typename cvec<T>::type;
+
+template <typename V> __device__ __forceinline__ V mk(decltype(V::x) a, decltype(V::x) b) { V r; r.x = a; r.y = b; return r; }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
+  return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
+template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
+// multiply by S*i (S = +1 or -1)
+template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
+  return S > 0 ? mk<V>(-a.y, a.x) : mk<V>(a.y, -a.x);
+}
+
+// ---------------------------------------------------------------------------
+// compile-time cos/sin of 2 pi p / q (Taylor series after quadrant reduction)
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr double ce_sin_q(double x) {
+  double term = x, sum = x;
+  for (int k = 1; k < 24; ++k) { term *= -x * x / ((2.0 * k) * (2.0 * k + 1.0)); sum += term; }
+  return sum;
+}
+__host__ __device__ constexpr double ce_cos_q(double x) {
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 24; ++k) { term *= -x * x / ((2.0 * k - 1.0) * (2.0 * k)); sum += term; }
+  return sum;
+}
+// angle 2 pi p/q = quadrant*pi/2 + (pi/2) rem/q
+__host__ __device__ constexpr double ce_cos2pi(long p, long q) {
+  long a = ((p % q) + q) % q;
+  long qd = (4 * a) / q;
+  long rem = 4 * a - qd * q;
+  double th = 1.5707963267948966192 * (double)rem / (double)q;
+  double c = ce_cos_q(th), s = ce_sin_q(th);
+  return qd == 0 ? c : qd == 1 ? -s : qd == 2 ? -c : s;
+}
+__host__ __device__ constexpr double ce_sin2pi(long p, long q) {
+  long a = ((p % q) + q) % q;
+  long qd = (4 * a) / q;
+  long rem = 4 * a - qd * q;
+  double th = 1.5707963267948966192 * (double)rem / (double)q;
+  double c = ce_cos_q(th), s = ce_sin_q(th);
+  return qd == 0 ? s : qd == 1 ? c : qd == 2 ? -s : -c;
+}
+
+template <int... Is, class F>
+__device__ __forceinline__ void sfor_impl(std::integer_sequence<int, Is...>, F&& f) {
+  (f(std::integral_constant<int, Is>{}), ...);
+}
+template <int N, class F> __device__ __forceinline__ void sfor(F&& f) {
+  sfor_impl(std::make_integer_sequence<int, N>{}, f);
+}
+
+// ---------------------------------------------------------------------------
+// small DFTs in registers: a[0..R) -> DFT_R(a) in natural order, sign S
+// (S = -1: exp(-2 pi i jk/R), analysis; S = +1: synthesis, unscaled)
+// ---------------------------------------------------------------------------
+template <int R, int S> struct Dft;
+
+template <int S> struct Dft<2, S> {
+  template <typename V> __device__ __forceinline__ static void run(V* a) {
+    V t = a[0];
+    a[0] = t + a[1];
+    a[1] = t - a[1];
+  }
+};
+
+template <int S> struct Dft<3, S> {
+  template <typename V> __device__ __forceinline__ static void run(V* a) {
+    using T = decltype(V::x);
+    constexpr T h = (T)0.86602540378443864676;  // sin(2 pi/3)
+    V t = a[1] + a[2];
+    V d = a[1] - a[2];
+    V m = mk<V>(a[0].x - (T)0.5 * t.x, a[0].y - (T)0.5 * t.y);
+    V r = mul_si<S>(cscale(d, h));
+    a[0] = a[0] + t;
+    a[1] = m + r;
+    a[2] = m - r;
+  }
+};
+
+template <int S> struct Dft<4, S> {
+  template <typename V> __device__ __forceinline__ static void run(V* a) {
+    V s02 = a[0] + a[2], d02 = a[0] - a[2];
+    V s13 = a[1] + a[3], d13 = mul_si<S>(a[1] - a[3]);
+    a[0] = s02 + s13;
+    a[2] = s02 - s13;
+    a[1] = d02 + d13;
+    a[3] = d02 - d13;
+  }
+};
+
+template <int S> struct Dft<5, S> {
+  template <typename V> __device__ __forceinline__ static void run(V* a) {
+    using T = decltype(V::x);
+    constexpr T c1 = (T)ce_cos2pi(1, 5), c2 = (T)ce_cos2pi(2, 5);
+    constexpr T s1 = (T)ce_sin2pi(1, 5), s2 = (T)ce_sin2pi(2, 5);
+    V t1 = a[1] + a[4], d1 = a[1] - a[4];
+    V t2 = a[2] + a[3], d2 = a[2] - a[3];
+    V m1 = mk<V>(a[0].x + c1 * t1.x + c2 * t2.x, a[0].y + c1 * t1.y + c2 * t2.y);
+    V m2 = mk<V>(a[0].x + c2 * t1.x + c1 * t2.x, a[0].y + c2 * t1.y + c1 * t2.y);
+    V r1 = mul_si<S>(mk<V>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
+    V r2 = mul_si<S>(mk<V>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
+    a[0] = a[0] + t1 + t2;
+    a[1] = m1 + r1;
+    a[4] = m1 - r1;
+    a[2] = m2 + r2;
+    a[3] = m2 - r2;
+  }
+};
+
+// composite R = R1 * R2: index j = R2 j1 + j2, output k = k1 + R1 k2
+//   b[j2][k1] = DFT_R1 over j1 of a[R2 j1 + j2];  b *= w_R^(S j2 k1);
+//   y[k1 + R1 k2] = DFT_R2 over j2 of b[j2][k1]
+template <int R1, int R2, int S> struct DftComposite {
+  template <typename V> __device__ __forceinline__ static void run(V* a) {
+    using T = decltype(V::x);
+    constexpr int R = R1 * R2;
+    V b[R];
+    sfor<R2>([&](auto J2) {
+      constexpr int j2 = decltype(J2)::value;
+      V col[R1];
+      sfor<R1>([&](auto J1) { constexpr int j1 = decltype(J1)::value; col[j1] = a[R2 * j1 + j2]; });
+      Dft<R1, S>::run(col);
+      sfor<R1>([&](auto K1) {
+        constexpr int k1 = decltype(K1)::value;
+        constexpr int e = (j2 * k1) % R;
+        if constexpr (e == 0) {
+          b[j2 * R1 + k1] = col[k1];
+        } else {
+          constexpr T c = (T)ce_cos2pi(e, R);
+          constexpr T s = (T)(S * ce_sin2pi(e, R));
+          b[j2 * R1 + k1] = cmul(col[k1], mk<V>(c, s));
+        }
+      });
+    });
+    sfor<R1>([&](auto K1) {
+      constexpr int k1 = decltype(K1)::value;
+      V row[R2];
+      sfor<R2>([&](auto J2) { constexpr int j2 = decltype(J2)::value; row[j2] = b[j2 * R1 + k1]; });
+      Dft<R2, S>::run(row);
+      sfor<R2>([&](auto K2) { constexpr int k2 = decltype(K2)::value; a[k1 + R1 * k2] = row[k2]; });
+    });
+  }
+};
+template <int S> struct Dft<8, S> : DftComposite<2, 4, S> {};
+template <int S> struct Dft<16, S> : DftComposite<4, 4, S> {};
+
+// items held in registers per thread for one stage of radix R (~16 complex)
+__host__ __device__ constexpr int ipt_for(int R) {
+  return R >= 16 ? 1 : R >= 8 ? 2 : R >= 5 ? 3 : R == 4 ? 4 : R == 3 ? 5 : 8;
+}
+
+constexpr int kMaxStages = 12;
+
+// Runtime description of one transform length: radices in stage order.
+struct RadixPlan {
+  int m;
+  int nst;
+  int r[kMaxStages];
+  int pad_shift;  // smem index e -> e + (e >> pad_shift); 30 = no padding
+};
+
+template <typename V> struct SmemIO {
+  V* sm;
+  int nbs;
+  int pad_shift;
+  __device__ __forceinline__ int addr(int b, int i) const {
+    int e = (i << nbs) + b;
+    return e + (e >> pad_shift);
+  }
+  __device__ __forceinline__ V get(int b, int i) const { return sm[addr(b, i)]; }
+  __device__ __forceinline__ void put(int b, int i, V v) const { sm[addr(b, i)] = v; }
+};
+
+// One Stockham stage over nb = 2^nbs interleaved transforms of length m.
+// tw[t * twstride] = exp(-2 pi i t / m).  When src and dst are the same
+// shared buffer (inplace) every thread holds all its items in registers
+// across a barrier.
+template <int R, int S, typename V, class Src, class Dst>
+__device__ __forceinline__ void stockham_stage(int m, int Ns, int nbs, const V* __restrict__ tw, int twstride,
+                                               const Src& src, const Dst& dst, bool inplace) {
+  constexpr int IPT = ipt_for(R);
+  const int mR = m / R;
+  const int items = mR << nbs;
+  const int bmask = (1 << nbs) - 1;
+  const int tstep = (m / (Ns * R)) * twstride;
+  V a[IPT][R];
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    const int w = threadIdx.x + q * blockDim.x;
+    if (w < items) {
+      const int b = w & bmask, j = w >> nbs;
+#pragma unroll
+      for (int i = 0; i < R; ++i) a[q][i] = src.get(b, j + i * mR);
+      if (Ns > 1) {
+        const int k = j % Ns;
+#pragma unroll
+        for (int i = 1; i < R; ++i) {
+          V t = __ldg(&tw[i * k * tstep]);
+          if (S > 0) t.y = -t.y;
+          a[q][i] = cmul(a[q][i], t);
+        }
+      }
+      Dft<R, S>::run(a[q]);
+    }
+  }
+  if (inplace) __syncthreads();
+#pragma unroll
+  for (int q = 0; q < IPT; ++q) {
+    const int w = threadIdx.x + q * blockDim.x;
+    if (w < items) {
+      const int b = w & bmask, j = w >> nbs;
+      const int k = j % Ns;
+      const int base = (j / Ns) * Ns * R + k;
+#pragma unroll
+      for (int i = 0; i < R; ++i) dst.put(b, base + i * Ns, a[q][i]);
+    }
+  }
+}
+
+template <int S, typename V, class Src, class Dst>
+__device__ __forceinline__ void stage_dispatch(int R, int m, int Ns, int nbs, const V* tw, int twstride,
+                                               const Src& src, const Dst& dst, bool inplace) {
+  switch (R) {
+    case 16: stockham_stage<16, S>(m, Ns, nbs, tw, twstride, src, dst, inplace); break;
+    case 8: stockham_stage<8, S>(m, Ns, nbs, tw, twstride, src, dst, inplace); break;
+    case 5: stockham_stage<5, S>(m, Ns, nbs, tw, twstride, src, dst, inplace); break;
+    case 4: stockham_stage<4, S>(m, Ns, nbs, tw, twstride, src, dst, inplace); break;
+    case 3: stockham_stage<3, S>(m, Ns, nbs, tw, twstride, src, dst, inplace); break;
+    default: stockham_stage<2, S>(m, Ns, nbs, tw, twstride, src, dst, inplace); break;
+  }
+}
+
+// Whole transform: load -> [smem stages] -> store.  The caller's block size
+// must cover every stage (blockDim.x * ipt_for(r_s) >= (m / r_s) << nbs).
+// Ends without a trailing barrier; a caller that reuses `sm` must sync first.
+template <int S, typename V, class Load, class Store>
+__device__ __forceinline__ void block_fft(const RadixPlan& rp, int nbs, V* sm, const V* tw, int twstride,
+                                          const Load& load, const Store& store) {
+  if (rp.nst == 1) {
+    stage_dispatch<S>(rp.r[0], rp.m, 1, nbs, tw, twstride, load, store, false);
+    return;
+  }
+  SmemIO<V> io{sm, nbs, rp.pad_shift};
+  stage_dispatch<S>(rp.r[0], rp.m, 1, nbs, tw, twstride, load, io, false);
+  __syncthreads();
+  int Ns = rp.r[0];
+  for (int s = 1; s + 1 < rp.nst; ++s) {
+    stage_dispatch<S>(rp.r[s], rp.m, Ns, nbs, tw, twstride, io, io, true);
+    __syncthreads();
+    Ns *= rp.r[s];
+  }
+  stage_dispatch<S>(rp.r[rp.nst - 1], rp.m, Ns, nbs, tw, twstride, io, store, false);
+}
+
+}  // namespace qtam

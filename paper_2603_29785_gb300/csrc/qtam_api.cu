@@ -1,0 +1,772 @@
+// Host side of the QTAM library: plan construction (filter-bank geometry,
+// FP64 frame operator, twiddle tables, launch shapes) and the C ABI.
+//
+// Geometry follows App. A of the paper: a log grid of centre frequencies per
+// Q-plane, window length proportional to f_k N_t / Q clamped at
+// L_max = 2 floor(ceil(N_t Delta f_max) / 2) + 1 (Delta f_max = largest gap
+// between neighbouring centres, or a manual clamp), centre bin k_c = f_k N_t
+// (Eq. support), bisquare windows (Eq. gwpy_window_formula) and an envelope
+// length M no shorter than the largest window (Sec. III, lossless
+// decimation).  Where the paper leaves a constant open the choices are:
+// h = max(1, min(floor(f T q_width / Q), h_max)) with q_width = sqrt(11);
+// k_c rounds half away from zero; M = smallest 2^a 3^b 5^c >= max L;
+// c_k normalises the untruncated window to unit energy (L2, default), to
+// 1 / sum W'^2 (PAPER) or 1 (NONE); windows are cut to 0 <= f <= N/2.
+//
+// The frame operator P[f] = sum_k W_k[f]^2 (App. C) and its inverse on the
+// kept set F_tau = {P > 0, P >= tau max P} are the only FP64 arithmetic of
+// the library, done here once per plan (and once per new plane mask).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/qtam.h"
+#include "qtam_internal.h"
+
+using namespace qtam;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+qtam_status fail(qtam_status s, const std::string& msg) {
+  g_last_error = msg;
+  return s;
+}
+qtam_status fail_cuda(cudaError_t e, const char* where) {
+  g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return QTAM_ERR_CUDA;
+}
+
+constexpr int kMaxSmem = 227 * 1024;
+constexpr int kMaxThreads = 512;  // must match the kernels' __launch_bounds__
+
+bool factor235(int64_t m, int& a, int& b, int& c) {
+  a = b = c = 0;
+  if (m < 1) return false;
+  while (m % 2 == 0) { m /= 2; ++a; }
+  while (m % 3 == 0) { m /= 3; ++b; }
+  while (m % 5 == 0) { m /= 5; ++c; }
+  return m == 1;
+}
+
+bool make_radix_plan(int m, RadixPlan& rp) {
+  int a, b, c;
+  if (m < 2 || !factor235(m, a, b, c)) return false;
+  std::vector<int> rs;
+  while (a >= 4) { rs.push_back(16); a -= 4; }
+  if (a == 3) rs.push_back(8);
+  else if (a == 2) rs.push_back(4);
+  else if (a == 1) rs.push_back(2);
+  for (int i = 0; i < c; ++i) rs.push_back(5);
+  for (int i = 0; i < b; ++i) rs.push_back(3);
+  if ((int)rs.size() > kMaxStages) return false;
+  std::memset(&rp, 0, sizeof(rp));
+  rp.m = m;
+  rp.nst = (int)rs.size();
+  for (int i = 0; i < rp.nst; ++i) rp.r[i] = rs[i];
+  const int r0 = rs[0];
+  rp.pad_shift = (r0 & (r0 - 1)) == 0 ? 4 : 30;
+  return true;
+}
+
+int threads_for(const RadixPlan& rp, int nbs) {
+  int t = 32;
+  for (int s = 0; s < rp.nst; ++s) {
+    const int items = (rp.m / rp.r[s]) << nbs;
+    const int ipt = ipt_for(rp.r[s]);
+    t = std::max(t, (items + ipt - 1) / ipt);
+  }
+  return (t + 31) / 32 * 32;
+}
+
+size_t smem_for(const RadixPlan& rp, int nbs, size_t elem) {
+  if (rp.nst <= 1) return 0;
+  const size_t e = (size_t)rp.m << nbs;
+  return (e + (e >> rp.pad_shift) + 1) * elem;
+}
+
+int64_t smooth_at_least(int64_t n) {
+  for (int64_t m = std::max<int64_t>(1, n);; ++m) {
+    int a, b, c;
+    if (factor235(m, a, b, c)) return m;
+  }
+}
+
+// unnormalised bisquare W'(d) = (1 - (d/h)^2)^2, |d| <= h
+inline double bisq(int64_t d, int64_t h) {
+  const int64_t a = d < 0 ? -d : d;
+  if (a > h) return 0.0;
+  const double u = (double)((h - a) * (h + a)) / ((double)h * (double)h);
+  return u * u;
+}
+
+struct MaskEntry {
+  void* invP = nullptr;   // [Nr] T
+  int* rows = nullptr;    // selected row indices
+  int n_sel = 0;
+  int64_t kept = 0;
+  double kappa = 0;
+};
+
+}  // namespace
+
+struct qtam_plan_s {
+  // description
+  double fs = 0;
+  int64_t N = 0;
+  std::vector<double> q;
+  double fmin = 0, fmax = 0;
+  int K = 0;
+  int norm = QTAM_NORM_L2;
+  double q_width = 0;
+  double max_window_hz = 0;
+  int compute = QTAM_DTYPE_F32;
+  int env = QTAM_DTYPE_F32;
+  double tau = 0;
+  // geometry
+  int P = 0;
+  int64_t n = 0, Nr = 0;
+  int M = 0;
+  int64_t h_max = 0;
+  int Lmax = 0;
+  int64_t band_bins = 0;
+  std::vector<double> f, c;
+  std::vector<int64_t> kc;
+  std::vector<int> h;
+  std::vector<std::vector<double>> Pplane;  // per-plane frame operator
+  // device
+  int device = -1;
+  LongCfg lc{};
+  RowCfg rc{};
+  void* d_rows = nullptr;
+  void* d_twM = nullptr;
+  void* d_twn = nullptr;
+  void* d_twN = nullptr;
+  size_t device_bytes = 0;
+  std::mutex mu;
+  std::map<uint64_t, MaskEntry> masks;
+
+  size_t real_size() const { return compute == QTAM_DTYPE_F64 ? 8 : 4; }
+  size_t cplx_size() const { return 2 * real_size(); }
+  size_t env_size() const {
+    return env == QTAM_DTYPE_F64 ? 16 : (env == QTAM_DTYPE_F32 ? 8 : 4);
+  }
+  uint64_t all_mask() const { return P >= 64 ? ~0ull : ((1ull << P) - 1); }
+};
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+template <typename T> void fill_twiddles(std::vector<T>& v, int64_t len, int64_t count) {
+  // e^{-2 pi i t / len}, t < count, evaluated in FP64
+  v.resize(2 * count);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int64_t t = 0; t < count; ++t) {
+    const double ang = two_pi * (double)t / (double)len;
+    v[2 * t] = (T)std::cos(ang);
+    v[2 * t + 1] = (T)(-std::sin(ang));
+  }
+}
+
+qtam_status upload(void** dst, const void* src, size_t bytes, size_t& total) {
+  cudaError_t e = cudaMalloc(dst, bytes);
+  if (e != cudaSuccess) return fail(QTAM_ERR_OUT_OF_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  total += bytes;
+  e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaMemcpy");
+  return QTAM_OK;
+}
+
+// Build (or find) the normaliser and row list for a plane mask.  Called with plan->mu held.
+qtam_status build_mask(qtam_plan_s* pl, uint64_t mask, MaskEntry** out) {
+  auto it = pl->masks.find(mask);
+  if (it != pl->masks.end()) {
+    *out = &it->second;
+    return QTAM_OK;
+  }
+  std::vector<double> Pm(pl->Nr, 0.0);
+  std::vector<int> rows;
+  for (int p = 0; p < pl->P; ++p) {
+    if (!((mask >> p) & 1ull)) continue;
+    for (int64_t f = 0; f < pl->Nr; ++f) Pm[f] += pl->Pplane[p][f];
+    for (int k = 0; k < pl->K; ++k) rows.push_back(p * pl->K + k);
+  }
+  double pmax = 0;
+  for (double v : Pm) pmax = std::max(pmax, v);
+  MaskEntry e;
+  std::vector<double> inv(pl->Nr, 0.0);
+  for (int64_t f = 0; f < pl->Nr; ++f) {
+    if (Pm[f] > 0 && Pm[f] >= pl->tau * pmax) {
+      inv[f] = 1.0 / Pm[f];
+      ++e.kept;
+    }
+  }
+  if (e.kept == 0) return fail(QTAM_ERR_NO_COVERAGE, "the selected planes cover no frequency bin");
+  // kappa = max over kept bins of max_k W_k / P
+  std::vector<double> wmax(pl->Nr, 0.0);
+  for (int r : rows) {
+    const int64_t hk = pl->h[r], kc = pl->kc[r];
+    for (int64_t d = -hk; d <= hk; ++d) {
+      const int64_t fb = kc + d;
+      if (fb < 0 || fb >= pl->Nr) continue;
+      wmax[fb] = std::max(wmax[fb], pl->c[r] * bisq(d, hk));
+    }
+  }
+  for (int64_t f = 0; f < pl->Nr; ++f)
+    if (inv[f] > 0) e.kappa = std::max(e.kappa, wmax[f] * inv[f]);
+  e.n_sel = (int)rows.size();
+  if (pl->device >= 0) {
+    size_t tot = 0;
+    qtam_status s;
+    if (pl->compute == QTAM_DTYPE_F64) {
+      s = upload(&e.invP, inv.data(), inv.size() * sizeof(double), tot);
+    } else {
+      std::vector<float> invf(inv.begin(), inv.end());
+      s = upload(&e.invP, invf.data(), invf.size() * sizeof(float), tot);
+    }
+    if (s != QTAM_OK) return s;
+    s = upload(reinterpret_cast<void**>(&e.rows), rows.data(), rows.size() * sizeof(int), tot);
+    if (s != QTAM_OK) {
+      cudaFree(e.invP);
+      return s;
+    }
+    pl->device_bytes += tot;
+  }
+  auto res = pl->masks.emplace(mask, e);
+  *out = &res.first->second;
+  return QTAM_OK;
+}
+
+bool choose_long(int64_t n, bool dbl, LongCfg& lc) {
+  if (n < 4 || n > (int64_t)1 << 26) return false;
+  const size_t elem = dbl ? 16 : 8;
+  double best = 1e30;
+  bool found = false;
+  for (int64_t n1 = 2; n1 <= n / 2; ++n1) {
+    if (n % n1) continue;
+    const int64_t n2 = n / n1;
+    RadixPlan r1, r2;
+    if (!make_radix_plan((int)n1, r1) || !make_radix_plan((int)n2, r2)) continue;
+    int cn = dbl ? 3 : 4, rn = dbl ? 1 : 2;
+    while (cn > 0 && n2 % (1 << cn)) --cn;
+    while (rn > 0 && n1 % (1 << rn)) --rn;
+    const int t1 = threads_for(r1, cn), t2 = threads_for(r2, rn);
+    const size_t s1 = smem_for(r1, cn, elem), s2 = smem_for(r2, rn, elem);
+    if (t1 > kMaxThreads || t2 > kMaxThreads || s1 > (size_t)kMaxSmem || s2 > (size_t)kMaxSmem) continue;
+    // prefer balanced splits and full-width column groups
+    const double score = std::fabs(std::log2((double)n1) - std::log2((double)n2) + 1.0) + (cn < (dbl ? 3 : 4) ? 4 : 0) +
+                         (rn < (dbl ? 1 : 2) ? 2 : 0);
+    if (score < best) {
+      best = score;
+      found = true;
+      lc.n = (int)n;
+      lc.n1 = (int)n1;
+      lc.n2 = (int)n2;
+      lc.col_nbs = cn;
+      lc.row_nbs = rn;
+      lc.rp1 = r1;
+      lc.rp2 = r2;
+      lc.col_threads = t1;
+      lc.row_threads = t2;
+      lc.col_smem = s1;
+      lc.row_smem = s2;
+    }
+  }
+  return found;
+}
+
+template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
+  std::vector<T> tw;
+  size_t tot = 0;
+  qtam_status s;
+  fill_twiddles(tw, pl->M, pl->M);
+  if ((s = upload(&pl->d_twM, tw.data(), tw.size() * sizeof(T), tot)) != QTAM_OK) return s;
+  fill_twiddles(tw, pl->n, pl->n);
+  if ((s = upload(&pl->d_twn, tw.data(), tw.size() * sizeof(T), tot)) != QTAM_OK) return s;
+  fill_twiddles(tw, pl->N, pl->n / 2 + 1);
+  if ((s = upload(&pl->d_twN, tw.data(), tw.size() * sizeof(T), tot)) != QTAM_OK) return s;
+  std::vector<RowDev<T>> rows(pl->P * pl->K);
+  const double sMN = std::sqrt((double)pl->M * (double)pl->N), sNM = std::sqrt((double)pl->N / (double)pl->M);
+  for (size_t r = 0; r < rows.size(); ++r) {
+    rows[r].kc = (int)pl->kc[r];
+    rows[r].h = pl->h[r];
+    rows[r].c_fwd = (T)(pl->c[r] / sMN);
+    rows[r].c_inv = (T)(pl->c[r] * sNM);
+    rows[r].inv_h2 = (T)(1.0 / ((double)pl->h[r] * (double)pl->h[r]));
+  }
+  if ((s = upload(&pl->d_rows, rows.data(), rows.size() * sizeof(RowDev<T>), tot)) != QTAM_OK) return s;
+  pl->device_bytes += tot;
+  return QTAM_OK;
+}
+
+void free_plan(qtam_plan_s* pl) {
+  if (!pl) return;
+  if (pl->device >= 0) {
+    DeviceGuard g(pl->device);
+    cudaFree(pl->d_rows);
+    cudaFree(pl->d_twM);
+    cudaFree(pl->d_twn);
+    cudaFree(pl->d_twN);
+    for (auto& kv : pl->masks) {
+      cudaFree(kv.second.invP);
+      cudaFree(kv.second.rows);
+    }
+  }
+  delete pl;
+}
+
+qtam_status check_mask(const qtam_plan_s* pl, uint64_t& mask) {
+  if (mask == 0) mask = pl->all_mask();
+  if (mask & ~pl->all_mask()) return fail(QTAM_ERR_INVALID_ARG, "plane_mask selects planes the plan does not have");
+  return QTAM_OK;
+}
+
+size_t ws_bytes(const qtam_plan_s* pl, int64_t B) {
+  const size_t cs = pl->cplx_size();
+  const size_t r0 = ((size_t)B * pl->Nr * cs + 255) / 256 * 256;
+  return r0 + (size_t)B * pl->n * cs;
+}
+
+struct Regions {
+  void* r0;  // [B][Nr] complex: U (stride n) then X / A (stride Nr)
+  void* r1;  // [B][n] complex: Z / V
+};
+Regions split_ws(const qtam_plan_s* pl, void* ws, int64_t B) {
+  const size_t cs = pl->cplx_size();
+  const size_t r0 = ((size_t)B * pl->Nr * cs + 255) / 256 * 256;
+  return Regions{ws, static_cast<char*>(ws) + r0};
+}
+
+qtam_status common_checks(const qtam_plan_s* pl, int64_t batch) {
+  if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
+  if (pl->device < 0) return fail(QTAM_ERR_NO_DEVICE, "host-only plan (device = -1) cannot run transforms");
+  if (batch < 0) return fail(QTAM_ERR_INVALID_ARG, "batch < 0");
+  if (batch * (int64_t)pl->P * pl->K > INT32_MAX) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "batch * rows exceeds 2^31-1");
+  return QTAM_OK;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+template <typename T>
+qtam_status run_spectrum(qtam_plan_s* pl, const void* x, int64_t B, void* X, void* ws, cudaStream_t st) {
+  using V = cplx<T>;
+  Regions rg = split_ws(pl, ws, B);
+  cudaError_t e = launch_spectrum<T>(pl->lc, static_cast<const V*>(x), static_cast<V*>(rg.r0), static_cast<V*>(rg.r1),
+                                     static_cast<V*>(X), B, static_cast<const V*>(pl->d_twn),
+                                     static_cast<const V*>(pl->d_twN), st);
+  return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "spectrum launch");
+}
+
+template <typename T> qtam_status run_envelopes(qtam_plan_s* pl, const void* X, int64_t B, void* y, cudaStream_t st) {
+  using V = cplx<T>;
+  cudaError_t e = launch_rows_forward<T>(pl->rc, static_cast<const RowDev<T>*>(pl->d_rows), pl->P * pl->K, pl->Nr,
+                                         static_cast<const V*>(X), y, pl->env, B, static_cast<const V*>(pl->d_twM), st);
+  return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "envelope launch");
+}
+
+template <typename T>
+qtam_status run_accumulate(qtam_plan_s* pl, const void* y, int64_t B, const MaskEntry* me, void* A, cudaStream_t st) {
+  using V = cplx<T>;
+  cudaError_t e = cudaMemsetAsync(A, 0, (size_t)B * pl->Nr * sizeof(V), st);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync");
+  e = launch_rows_inverse<T>(pl->rc, static_cast<const RowDev<T>*>(pl->d_rows), me->rows, me->n_sel, pl->P * pl->K,
+                             pl->Nr, y, pl->env, static_cast<V*>(A), B, static_cast<const V*>(pl->d_twM), st);
+  return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "accumulate launch");
+}
+
+template <typename T>
+qtam_status run_synthesize(qtam_plan_s* pl, const void* A, int64_t B, const MaskEntry* me, void* x, void* ws,
+                           cudaStream_t st) {
+  using V = cplx<T>;
+  Regions rg = split_ws(pl, ws, B);
+  cudaError_t e = launch_synthesis<T>(pl->lc, static_cast<const V*>(A), static_cast<const T*>(me->invP),
+                                      static_cast<V*>(rg.r1), static_cast<V*>(x), B, static_cast<const V*>(pl->d_twn),
+                                      static_cast<const V*>(pl->d_twN), st);
+  return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "synthesis launch");
+}
+
+qtam_status get_mask(qtam_plan_s* pl, uint64_t mask, MaskEntry** me) {
+  qtam_status s = check_mask(pl, mask);
+  if (s != QTAM_OK) return s;
+  DeviceGuard g(pl->device);
+  std::lock_guard<std::mutex> lk(pl->mu);
+  return build_mask(pl, mask, me);
+}
+
+}  // namespace
+
+extern "C" {
+
+void qtam_plan_desc_init(qtam_plan_desc* d) {
+  if (!d) return;
+  std::memset(d, 0, sizeof(*d));
+  d->window = QTAM_WIN_BISQUARE;
+  d->norm = QTAM_NORM_L2;
+  d->q_width = 0.0;
+  d->max_window_hz = 0.0;
+  d->n_out = 0;
+  d->compute_dtype = QTAM_DTYPE_F32;
+  d->envelope_dtype = QTAM_DTYPE_F32;
+  d->p_floor_rel = -1.0;
+}
+
+qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
+  if (!d || !out) return fail(QTAM_ERR_INVALID_ARG, "desc or out is NULL");
+  *out = nullptr;
+  if (!(d->sample_rate > 0) || d->length <= 0 || d->length % 2) return fail(QTAM_ERR_INVALID_ARG, "sample_rate > 0 and an even length > 0 are required");
+  if (!d->q || d->n_q < 1 || d->n_q > 64) return fail(QTAM_ERR_INVALID_ARG, "1 to 64 Q values are required");
+  for (int i = 0; i < d->n_q; ++i)
+    if (!(d->q[i] > 0)) return fail(QTAM_ERR_INVALID_ARG, "Q values must be > 0");
+  if (d->rows_per_plane < 1) return fail(QTAM_ERR_INVALID_ARG, "rows_per_plane >= 1 required");
+  if (!(d->f_min > 0) || !(d->f_max >= d->f_min)) return fail(QTAM_ERR_INVALID_ARG, "0 < f_min <= f_max required");
+  if (d->rows_per_plane > 1 && !(d->f_max > d->f_min)) return fail(QTAM_ERR_INVALID_ARG, "f_max > f_min required for K > 1");
+  if (d->window != QTAM_WIN_BISQUARE) return fail(QTAM_ERR_INVALID_ARG, "unknown window");
+  if (d->norm < QTAM_NORM_L2 || d->norm > QTAM_NORM_NONE) return fail(QTAM_ERR_INVALID_ARG, "unknown norm");
+  if (d->compute_dtype != QTAM_DTYPE_F32 && d->compute_dtype != QTAM_DTYPE_F64) return fail(QTAM_ERR_INVALID_ARG, "compute_dtype must be F32 or F64");
+  if (d->compute_dtype == QTAM_DTYPE_F64 && d->envelope_dtype != QTAM_DTYPE_F64) return fail(QTAM_ERR_INVALID_ARG, "F64 compute stores F64 envelopes");
+  if (d->compute_dtype == QTAM_DTYPE_F32 && d->envelope_dtype == QTAM_DTYPE_F64) return fail(QTAM_ERR_INVALID_ARG, "F64 envelopes need F64 compute");
+  if (d->envelope_dtype < 0 || d->envelope_dtype > QTAM_DTYPE_F16) return fail(QTAM_ERR_INVALID_ARG, "unknown envelope dtype");
+  if (d->max_window_hz < 0 || d->n_out < 0) return fail(QTAM_ERR_INVALID_ARG, "max_window_hz and n_out must be >= 0");
+  if (d->length > ((int64_t)1 << 27)) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "length above 2^27");
+
+  qtam_plan_s* pl = new (std::nothrow) qtam_plan_s();
+  if (!pl) return fail(QTAM_ERR_OUT_OF_MEMORY, "host allocation");
+  pl->fs = d->sample_rate;
+  pl->N = d->length;
+  pl->q.assign(d->q, d->q + d->n_q);
+  pl->fmin = d->f_min;
+  pl->fmax = d->f_max;
+  pl->K = d->rows_per_plane;
+  pl->norm = d->norm;
+  pl->q_width = d->q_width > 0 ? d->q_width : std::sqrt(11.0);
+  pl->max_window_hz = d->max_window_hz;
+  pl->compute = d->compute_dtype;
+  pl->env = d->envelope_dtype;
+  pl->tau = d->p_floor_rel >= 0 ? d->p_floor_rel : (pl->compute == QTAM_DTYPE_F64 ? 0.0 : 1e-6);
+  pl->P = d->n_q;
+  pl->n = pl->N / 2;
+  pl->Nr = pl->n + 1;
+
+  // --- grid and widths (App. A) ---
+  const double T = (double)pl->N / pl->fs;
+  std::vector<double> grid(pl->K);
+  for (int k = 0; k < pl->K; ++k)
+    grid[k] = pl->K == 1 ? pl->fmin : pl->fmin * std::pow(pl->fmax / pl->fmin, (double)k / (double)(pl->K - 1));
+  double dfmax = 0;
+  if (pl->max_window_hz > 0) dfmax = pl->max_window_hz;
+  else
+    for (int k = 0; k + 1 < pl->K; ++k) dfmax = std::max(dfmax, grid[k + 1] - grid[k]);
+  pl->h_max = dfmax > 0 ? (int64_t)std::ceil(T * dfmax) / 2 : ((int64_t)1 << 40);
+  const int R = pl->P * pl->K;
+  pl->f.resize(R);
+  pl->c.resize(R);
+  pl->kc.resize(R);
+  pl->h.resize(R);
+  int64_t Lmax = 0;
+  for (int p = 0; p < pl->P; ++p) {
+    for (int k = 0; k < pl->K; ++k) {
+      const int r = p * pl->K + k;
+      const double fk = grid[k];
+      pl->f[r] = fk;
+      pl->kc[r] = (int64_t)std::floor(fk * T + 0.5);
+      int64_t hi = (int64_t)std::floor(fk * T * pl->q_width / pl->q[p]);
+      hi = std::max<int64_t>(1, std::min(hi, pl->h_max));
+      if (hi > (int64_t)1 << 28) {
+        free_plan(pl);
+        return fail(QTAM_ERR_UNSUPPORTED_SIZE, "window half-width too large");
+      }
+      pl->h[r] = (int)hi;
+      double s2 = 0;
+      for (int64_t dd = -hi; dd <= hi; ++dd) {
+        const double w = bisq(dd, hi);
+        s2 += w * w;
+      }
+      pl->c[r] = pl->norm == QTAM_NORM_L2 ? 1.0 / std::sqrt(s2) : (pl->norm == QTAM_NORM_PAPER ? 1.0 / s2 : 1.0);
+      Lmax = std::max<int64_t>(Lmax, 2 * hi + 1);
+      if (pl->kc[r] > pl->n + hi || pl->kc[r] < -hi) {
+        free_plan(pl);
+        return fail(QTAM_ERR_INVALID_ARG, "a window lies wholly above Nyquist");
+      }
+    }
+  }
+  pl->Lmax = (int)Lmax;
+  if (d->n_out > 0) {
+    if (d->n_out < Lmax) {
+      free_plan(pl);
+      return fail(QTAM_ERR_ALIASING, "n_out is shorter than the largest window");
+    }
+    pl->M = d->n_out;
+  } else {
+    pl->M = (int)smooth_at_least(Lmax);
+  }
+
+  // --- frame operator per plane (App. C), FP64 ---
+  pl->Pplane.assign(pl->P, std::vector<double>(pl->Nr, 0.0));
+  pl->band_bins = 0;
+  for (int r = 0; r < R; ++r) {
+    const int p = r / pl->K;
+    const int64_t hk = pl->h[r], kcr = pl->kc[r];
+    for (int64_t dd = -hk; dd <= hk; ++dd) {
+      const int64_t fb = kcr + dd;
+      if (fb < 0 || fb >= pl->Nr) continue;
+      const double w = pl->c[r] * bisq(dd, hk);
+      pl->Pplane[p][fb] += w * w;
+      ++pl->band_bins;
+    }
+  }
+
+  // --- launch shapes ---
+  const bool dbl = pl->compute == QTAM_DTYPE_F64;
+  if (!make_radix_plan(pl->M, pl->rc.rp)) {
+    free_plan(pl);
+    return fail(QTAM_ERR_UNSUPPORTED_SIZE, "n_out must have no prime factor other than 2, 3, 5");
+  }
+  pl->rc.threads = threads_for(pl->rc.rp, 0);
+  pl->rc.smem = smem_for(pl->rc.rp, 0, pl->cplx_size());
+  if (pl->rc.threads > kMaxThreads || pl->rc.smem > (size_t)kMaxSmem) {
+    free_plan(pl);
+    return fail(QTAM_ERR_UNSUPPORTED_SIZE, "n_out too large for one thread block");
+  }
+  if (!choose_long(pl->n, dbl, pl->lc)) {
+    free_plan(pl);
+    return fail(QTAM_ERR_UNSUPPORTED_SIZE, "length/2 must be a product of 2, 3, 5 between 4 and 2^26");
+  }
+
+  pl->device = device;
+  if (device >= 0) {
+    DeviceGuard g(device);
+    if (!g.ok) {
+      pl->device = -1;
+      free_plan(pl);
+      return fail(QTAM_ERR_CUDA, "cudaSetDevice failed");
+    }
+    qtam_status s = dbl ? upload_tables<double>(pl) : upload_tables<float>(pl);
+    if (s != QTAM_OK) {
+      free_plan(pl);
+      return s;
+    }
+  }
+  MaskEntry* me = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(pl->mu);
+    qtam_status s;
+    if (device >= 0) {
+      DeviceGuard g(device);
+      s = build_mask(pl, pl->all_mask(), &me);
+    } else {
+      s = build_mask(pl, pl->all_mask(), &me);
+    }
+    if (s != QTAM_OK) {
+      free_plan(pl);
+      return s;
+    }
+  }
+  *out = pl;
+  return QTAM_OK;
+}
+
+qtam_status qtam_plan_info(qtam_plan_t pl, qtam_plan_info_t* o) {
+  if (!pl || !o) return fail(QTAM_ERR_INVALID_ARG, "NULL argument");
+  std::memset(o, 0, sizeof(*o));
+  o->length = pl->N;
+  o->n_bins = pl->Nr;
+  o->n_planes = pl->P;
+  o->rows_per_plane = pl->K;
+  o->n_out = pl->M;
+  o->h_max = (int32_t)std::min<int64_t>(pl->h_max, INT32_MAX);
+  o->max_window = pl->Lmax;
+  o->compute_dtype = pl->compute;
+  o->envelope_dtype = pl->env;
+  o->fft_n1 = pl->lc.n1;
+  o->fft_n2 = pl->lc.n2;
+  o->envelope_bytes_per_segment = (int64_t)pl->P * pl->K * pl->M * (int64_t)pl->env_size();
+  o->band_bins = pl->band_bins;
+  o->p_floor_rel = pl->tau;
+  std::lock_guard<std::mutex> lk(pl->mu);
+  auto it = pl->masks.find(pl->all_mask());
+  if (it != pl->masks.end()) {
+    o->kappa = it->second.kappa;
+    o->kept_bins = it->second.kept;
+  }
+  o->device_bytes = (int64_t)pl->device_bytes;
+  return QTAM_OK;
+}
+
+qtam_status qtam_plan_rows(qtam_plan_t pl, double* f, int64_t* kc, int32_t* h, double* c) {
+  if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
+  const size_t R = pl->f.size();
+  for (size_t r = 0; r < R; ++r) {
+    if (f) f[r] = pl->f[r];
+    if (kc) kc[r] = pl->kc[r];
+    if (h) h[r] = pl->h[r];
+    if (c) c[r] = pl->c[r];
+  }
+  return QTAM_OK;
+}
+
+qtam_status qtam_frame_operator(qtam_plan_t pl, uint64_t mask, double* p_out) {
+  if (!pl || !p_out) return fail(QTAM_ERR_INVALID_ARG, "NULL argument");
+  qtam_status s = check_mask(pl, mask);
+  if (s != QTAM_OK) return s;
+  std::fill(p_out, p_out + pl->Nr, 0.0);
+  for (int p = 0; p < pl->P; ++p)
+    if ((mask >> p) & 1ull)
+      for (int64_t fb = 0; fb < pl->Nr; ++fb) p_out[fb] += pl->Pplane[p][fb];
+  return QTAM_OK;
+}
+
+qtam_status qtam_workspace_size(qtam_plan_t pl, int64_t batch, size_t* bytes) {
+  if (!pl || !bytes || batch < 0) return fail(QTAM_ERR_INVALID_ARG, "bad argument");
+  *bytes = ws_bytes(pl, batch);
+  return QTAM_OK;
+}
+
+qtam_status qtam_stage_spectrum(qtam_plan_t pl, const void* x, int64_t B, void* X, void* ws, size_t wsb, void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK || B == 0) return s;
+  if (!x || !X || !ws) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (wsb < ws_bytes(pl, B)) return fail(QTAM_ERR_WORKSPACE, "workspace too small");
+  if (!aligned(x, pl->cplx_size()) || !aligned(X, pl->cplx_size()) || !aligned(ws, 256))
+    return fail(QTAM_ERR_INVALID_ARG, "x and X must be aligned to a complex element, workspace to 256 bytes");
+  DeviceGuard g(pl->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return pl->compute == QTAM_DTYPE_F64 ? run_spectrum<double>(pl, x, B, X, ws, st) : run_spectrum<float>(pl, x, B, X, ws, st);
+}
+
+qtam_status qtam_stage_envelopes(qtam_plan_t pl, const void* X, int64_t B, void* y, void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK || B == 0) return s;
+  if (!X || !y) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (!aligned(X, pl->cplx_size()) || !aligned(y, pl->env_size())) return fail(QTAM_ERR_INVALID_ARG, "misaligned buffer");
+  DeviceGuard g(pl->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return pl->compute == QTAM_DTYPE_F64 ? run_envelopes<double>(pl, X, B, y, st) : run_envelopes<float>(pl, X, B, y, st);
+}
+
+qtam_status qtam_stage_accumulate(qtam_plan_t pl, const void* y, int64_t B, uint64_t mask, void* A, void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK) return s;
+  MaskEntry* me = nullptr;
+  if ((s = get_mask(pl, mask, &me)) != QTAM_OK || B == 0) return s;
+  if (!y || !A) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (!aligned(A, pl->cplx_size()) || !aligned(y, pl->env_size())) return fail(QTAM_ERR_INVALID_ARG, "misaligned buffer");
+  DeviceGuard g(pl->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return pl->compute == QTAM_DTYPE_F64 ? run_accumulate<double>(pl, y, B, me, A, st) : run_accumulate<float>(pl, y, B, me, A, st);
+}
+
+qtam_status qtam_stage_synthesize(qtam_plan_t pl, const void* A, int64_t B, uint64_t mask, void* x, void* ws, size_t wsb,
+                                  void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK) return s;
+  MaskEntry* me = nullptr;
+  if ((s = get_mask(pl, mask, &me)) != QTAM_OK || B == 0) return s;
+  if (!A || !x || !ws) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (wsb < ws_bytes(pl, B)) return fail(QTAM_ERR_WORKSPACE, "workspace too small");
+  if (!aligned(A, pl->cplx_size()) || !aligned(x, pl->cplx_size()) || !aligned(ws, 256))
+    return fail(QTAM_ERR_INVALID_ARG, "misaligned buffer");
+  DeviceGuard g(pl->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  return pl->compute == QTAM_DTYPE_F64 ? run_synthesize<double>(pl, A, B, me, x, ws, st)
+                                       : run_synthesize<float>(pl, A, B, me, x, ws, st);
+}
+
+qtam_status qtam_forward(qtam_plan_t pl, const void* x, int64_t B, void* y, void* ws, size_t wsb, void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK || B == 0) return s;
+  if (!x || !y || !ws) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (wsb < ws_bytes(pl, B)) return fail(QTAM_ERR_WORKSPACE, "workspace too small");
+  if (!aligned(x, pl->cplx_size()) || !aligned(y, pl->env_size()) || !aligned(ws, 256))
+    return fail(QTAM_ERR_INVALID_ARG, "x must be aligned to two samples, y to one envelope element, workspace to 256 bytes");
+  DeviceGuard g(pl->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Regions rg = split_ws(pl, ws, B);
+  if (pl->compute == QTAM_DTYPE_F64) {
+    if ((s = run_spectrum<double>(pl, x, B, rg.r0, ws, st)) != QTAM_OK) return s;
+    return run_envelopes<double>(pl, rg.r0, B, y, st);
+  }
+  if ((s = run_spectrum<float>(pl, x, B, rg.r0, ws, st)) != QTAM_OK) return s;
+  return run_envelopes<float>(pl, rg.r0, B, y, st);
+}
+
+qtam_status qtam_inverse(qtam_plan_t pl, const void* y, int64_t B, uint64_t mask, void* x, void* ws, size_t wsb,
+                         void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK) return s;
+  MaskEntry* me = nullptr;
+  if ((s = get_mask(pl, mask, &me)) != QTAM_OK || B == 0) return s;
+  if (!x || !y || !ws) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (wsb < ws_bytes(pl, B)) return fail(QTAM_ERR_WORKSPACE, "workspace too small");
+  if (!aligned(x, pl->cplx_size()) || !aligned(y, pl->env_size()) || !aligned(ws, 256))
+    return fail(QTAM_ERR_INVALID_ARG, "misaligned buffer");
+  DeviceGuard g(pl->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Regions rg = split_ws(pl, ws, B);
+  if (pl->compute == QTAM_DTYPE_F64) {
+    if ((s = run_accumulate<double>(pl, y, B, me, rg.r0, st)) != QTAM_OK) return s;
+    return run_synthesize<double>(pl, rg.r0, B, me, x, ws, st);
+  }
+  if ((s = run_accumulate<float>(pl, y, B, me, rg.r0, st)) != QTAM_OK) return s;
+  return run_synthesize<float>(pl, rg.r0, B, me, x, ws, st);
+}
+
+qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, uint64_t mask, void* xhat_host,
+                                void* x_dev, void* y_dev, void* xhat_dev, void* ws, size_t wsb, void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK || B == 0) return s;
+  if (!x_host || !xhat_host) return fail(QTAM_ERR_INVALID_ARG, "NULL host buffer");
+  DeviceGuard g(pl->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t xb = (size_t)B * pl->N * pl->real_size();
+  cudaError_t e = cudaMemcpyAsync(x_dev, x_host, xb, cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) return fail_cuda(e, "host-to-device copy");
+  if ((s = qtam_forward(pl, x_dev, B, y_dev, ws, wsb, stream)) != QTAM_OK) return s;
+  if ((s = qtam_inverse(pl, y_dev, B, mask, xhat_dev, ws, wsb, stream)) != QTAM_OK) return s;
+  e = cudaMemcpyAsync(xhat_host, xhat_dev, xb, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return fail_cuda(e, "device-to-host copy");
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
+  return QTAM_OK;
+}
+
+qtam_status qtam_destroy(qtam_plan_t pl) {
+  free_plan(pl);
+  return QTAM_OK;
+}
+
+const char* qtam_status_string(qtam_status s) {
+  switch (s) {
+    case QTAM_OK: return "ok";
+    case QTAM_ERR_INVALID_ARG: return "invalid argument";
+    case QTAM_ERR_UNSUPPORTED_SIZE: return "unsupported size";
+    case QTAM_ERR_ALIASING: return "n_out shorter than the largest window (aliasing)";
+    case QTAM_ERR_NO_COVERAGE: return "no frequency bin is covered";
+    case QTAM_ERR_OUT_OF_MEMORY: return "out of memory";
+    case QTAM_ERR_CUDA: return "CUDA error";
+    case QTAM_ERR_TIMEOUT: return "device wait timed out";
+    case QTAM_ERR_NO_DEVICE: return "host-only plan";
+    case QTAM_ERR_WORKSPACE: return "workspace too small";
+  }
+  return "unknown status";
+}
+
+const char* qtam_last_error(void) { return g_last_error.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,68 @@
+// Internal declarations shared by the host plan code and the kernel files.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft_core.cuh"
+
+namespace qtam {
+
+constexpr int kMaxBlock = 512;   // threads per block of every FFT kernel
+
+// Opt a kernel into more than 48 KB of dynamic shared memory when needed.
+inline cudaError_t allow_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// One (plane, row) window on the device.  W_k(d) = c (((h-|d|)(h+|d|)) / h^2)^2.
+template <typename T> struct RowDev {
+  int kc;     // centre bin k_c
+  int h;      // half-width
+  T c_fwd;    // c_k / sqrt(M N): window normalisation times the forward renormalisation
+  T c_inv;    // c_k sqrt(N / M): window normalisation times the synthesis re-scaling
+  T inv_h2;   // 1 / h^2
+};
+
+// Long real FFT of N = 2n samples as an n = n1 * n2 four-step complex FFT.
+struct LongCfg {
+  int n;        // N / 2
+  int n1, n2;   // column length n1 (stride n2), row length n2
+  int col_nbs;  // log2 of columns per column-pass block
+  int row_nbs;  // log2 of rows per row-pass block
+  RadixPlan rp1, rp2;
+  int col_threads, row_threads;
+  size_t col_smem, row_smem;
+};
+
+struct RowCfg {
+  RadixPlan rp;  // radices of M
+  int threads;
+  size_t smem;
+};
+
+enum EnvKind { ENV_F32 = 0, ENV_F64 = 1, ENV_BF16 = 2, ENV_F16 = 3 };
+
+// ---- launchers (kernels_long.cu) ----
+// z: [B][n] complex view of the real input; U: [B][n]; Z: [B][n]; X: [B][n+1]
+template <typename T>
+cudaError_t launch_spectrum(const LongCfg& c, const cplx<T>* z, cplx<T>* U, cplx<T>* Z, cplx<T>* X, int64_t B,
+                            const cplx<T>* twn, const cplx<T>* twN, cudaStream_t st);
+// A: [B][n+1] accumulated spectrum; invP: [n+1]; V: [B][n] scratch; xout: [B][n] complex view of the output
+template <typename T>
+cudaError_t launch_synthesis(const LongCfg& c, const cplx<T>* A, const T* invP, cplx<T>* V, cplx<T>* xout, int64_t B,
+                             const cplx<T>* twn, const cplx<T>* twN, cudaStream_t st);
+
+// ---- launchers (kernels_rows.cu) ----
+// X: [B][Nr] spectrum -> y: [B][R][M] envelopes (R = P*K rows)
+template <typename T>
+cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_rows, int64_t Nr, const cplx<T>* X,
+                                void* y, int env, int64_t B, const cplx<T>* twM, cudaStream_t st);
+// y rows listed in row_list -> atomically accumulated into A: [B][Nr] (must be zeroed)
+template <typename T>
+cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const int* row_list, int n_sel, int n_rows,
+                                int64_t Nr, const void* y, int env, cplx<T>* A, int64_t B, const cplx<T>* twM,
+                                cudaStream_t st);
+
+}  // namespace qtam

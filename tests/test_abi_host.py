@@ -1,0 +1,111 @@
+"""The C-ABI library loads, exports every symbol include/qtam.h declares, and
+its host-side plan logic (App. A geometry, FP64 frame operator, argument
+checks) agrees with the oracle.  No GPU is needed: plans are made host-only
+(device = -1), and no transform is launched."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qtam_oracle as O
+from paper_2603_29785_gb300 import qtam
+
+
+@pytest.fixture(scope="module")
+def L():
+    return qtam.lib()
+
+
+def test_library_exports_every_header_symbol(L):
+    names = qtam.header_symbols()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(L, n), n
+        assert n in qtam.SIGNATURES, n
+
+
+def test_status_strings(L):
+    for s in range(10):
+        assert qtam.qtam_status_string(s) not in ("", "unknown status")
+
+
+CASES = [
+    dict(fs=4096, N=16384, qs=(8,), fmin=20, fmax=1024, K=64),
+    dict(fs=4096, N=262144, qs=(4, 8, 16, 32, 64), fmin=20, fmax=2048, K=128),
+    dict(fs=4096, N=32768, qs=(8, 16, 32), fmin=20, fmax=2048, K=128),
+    dict(fs=64.0, N=512, qs=(4.0, 8.0), fmin=3.0, fmax=30.0, K=12),
+    dict(fs=64.0, N=512, qs=(4.0, 8.0), fmin=3.0, fmax=30.0, K=12, norm="paper"),
+    dict(fs=64.0, N=512, qs=(2.0,), fmin=3.0, fmax=32.0, K=7, norm="none", max_window_hz=2.0),
+    dict(fs=256.0, N=1024, qs=(6.0, 12.0), fmin=2.0, fmax=100.0, K=20, n_out=96),
+    dict(fs=16384, N=16384 * 2, qs=(8, 16, 32), fmin=20, fmax=2048, K=128),
+]
+
+
+def _both(c):
+    kw = dict(norm=c.get("norm", "l2"), max_window_hz=c.get("max_window_hz", 0.0), n_out=c.get("n_out", 0))
+    g = O.geometry(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], **kw)
+    p = qtam.Plan(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], device=-1, **kw)
+    return g, p
+
+
+@pytest.mark.parametrize("i", range(len(CASES)))
+def test_geometry_matches_oracle(i):
+    g, p = _both(CASES[i])
+    assert p.M == g.M and p.info["max_window"] == int(g.L.max())
+    assert p.info["h_max"] == min(g.h_max, 2**31 - 1)
+    assert np.array_equal(p.geometry.kc, g.kc)
+    assert np.array_equal(p.geometry.h, g.h)
+    assert np.allclose(p.geometry.f, g.f, rtol=1e-14, atol=0)
+    assert np.allclose(p.geometry.c, g.c, rtol=1e-12, atol=0)
+
+
+@pytest.mark.parametrize("i", range(len(CASES)))
+def test_frame_operator_and_floor_match_oracle(i):
+    g, p = _both(CASES[i])
+    Pl = p.frame_operator(0)
+    Po = O.frame_operator(g)
+    assert np.max(np.abs(Pl - Po)) <= 1e-12 * np.max(Po)
+    tau = p.info["p_floor_rel"]
+    assert tau == 1e-6
+    assert p.info["kept_bins"] == int(O.kept_bins(Po, tau).sum())
+    assert p.info["kappa"] == pytest.approx(O.kappa(g, tau=tau), rel=1e-9)
+    if g.P > 1:
+        P1 = p.frame_operator(0b10)
+        assert np.max(np.abs(P1 - O.frame_operator(g, planes=[1]))) <= 1e-12 * np.max(Po)
+    assert p.info["band_bins"] == sum(O.band(g, a, b)[0].size for a in range(g.P) for b in range(g.K))
+
+
+def test_plan_info_sizes():
+    g, p = _both(CASES[1])
+    assert p.info["envelope_bytes_per_segment"] == 5 * 128 * 4800 * 8
+    assert p.info["fft_n1"] * p.info["fft_n2"] == g.N // 2
+    assert p.info["device_bytes"] == 0          # host-only: nothing uploaded
+    ws = qtam.qtam_workspace_size(p.handle, 64)
+    assert ws >= 64 * (g.N // 2 + g.Nr) * 8
+
+
+def _err(fn):
+    with pytest.raises(qtam.QtamError) as e:
+        fn()
+    return e.value.status
+
+
+def test_argument_errors():
+    assert _err(lambda: qtam.Plan(4096, 16383, (8,), 20, 1024, 64, device=-1)) == 1          # odd N
+    assert _err(lambda: qtam.Plan(4096, 16384, (), 20, 1024, 64, device=-1)) == 1            # no planes
+    assert _err(lambda: qtam.Plan(4096, 16384, (8,), 2000, 1024, 64, device=-1)) == 1        # fmin > fmax
+    assert _err(lambda: qtam.Plan(4096, 16384, (8,), 20, 1024, 64, n_out=100, device=-1)) == 3   # aliasing
+    assert _err(lambda: qtam.Plan(4096, 16384, (8,), 20, 1024, 64, n_out=251, device=-1)) == 2   # 251 is prime
+    assert _err(lambda: qtam.Plan(4096, 16384, (8,), 20, 1024, 64, compute="f64", envelope="bf16", device=-1)) == 1
+    assert _err(lambda: qtam.Plan(4096, 16384 + 14, (8,), 20, 1024, 64, device=-1)) == 2     # N/2 = 8199 = 3*2733
+    p = qtam.Plan(4096, 16384, (8,), 20, 1024, 64, device=-1)
+    assert _err(lambda: qtam.qtam_forward(p.handle, 0, 1, 0, 0, 0, 0)) == 8    # host-only plan
+    assert _err(lambda: qtam.qtam_frame_operator(p.handle, 0b110, p.Nr)) == 1  # plane 1, 2 do not exist
+    assert _err(lambda: qtam.qtam_workspace_size(p.handle, -1)) == 1
+
+
+def test_f64_defaults():
+    p = qtam.Plan(4096, 16384, (8,), 20, 1024, 64, compute="f64", device=-1)
+    assert p.info["p_floor_rel"] == 0.0 and p.info["envelope_bytes_per_segment"] == 64 * 250 * 16
+    g = O.geometry(4096, 16384, (8,), 20, 1024, 64)
+    assert p.info["kept_bins"] == int((O.frame_operator(g) > 0).sum())

@@ -1,0 +1,280 @@
+"""Parity of the CUDA path (called through the C ABI) with the FP64 oracle.
+
+Tolerances (FP32 compute), from the arithmetic: unit roundoff u = 6e-8; a
+mixed-radix FFT of length m has rms relative error ~ u sqrt(log2 m), the long
+FFT ~ u sqrt(log2 n), and the on-the-fly window ~ 3u, so the forward's
+relative Frobenius error is ~ 4e-7: bound 1e-6.  Element-wise, every
+coefficient must sit within 1e-5 of the segment's largest magnitude.  The
+round trip is bounded by 1e-5 relative to the oracle's projection onto the
+kept bins (the stated FP32 target).  FP64 compute: 1e-12 / 1e-13.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import qtam_oracle as O
+from paper_2603_29785_gb300 import qtam, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+FWD_FROB = {"f32": 1e-6, "f64": 1e-13}
+FWD_ELEM = {"f32": 1e-5, "f64": 1e-12}
+RT = {"f32": 1e-5, "f64": 1e-12}
+
+
+def dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def env_np(p, y):
+    y = host(y)
+    if p.envelope in ("bf16", "f16"):
+        y = y.astype(np.float64)
+        return y[..., 0] + 1j * y[..., 1]
+    return y.astype(np.complex128)
+
+
+def rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def elem_ok(a, b, tol):
+    return np.max(np.abs(a - b)) <= tol * np.max(np.abs(b))
+
+
+def geom_of(p):
+    return O.geometry(p._args["fs"], p._args["N"], p._args["qs"], p._args["fmin"], p._args["fmax"], p._args["K"],
+                      norm=p._args.get("norm", "l2"), max_window_hz=p._args.get("max_window_hz", 0.0),
+                      n_out=p._args.get("n_out", 0))
+
+
+def make(fs, N, qs, fmin, fmax, K, compute="f32", envelope=None, **kw):
+    p = qtam.Plan(fs, N, qs, fmin, fmax, K, compute=compute, envelope=envelope, device=0, **kw)
+    p._args = dict(fs=fs, N=N, qs=qs, fmin=fmin, fmax=fmax, K=K, **kw)
+    return p
+
+
+SMALL = [
+    dict(fs=64.0, N=512, qs=(4.0, 8.0), fmin=3.0, fmax=30.0, K=12),
+    dict(fs=64.0, N=256, qs=(1.0,), fmin=1.0, fmax=32.0, K=6),             # windows cut at DC and Nyquist
+    dict(fs=256.0, N=1024, qs=(6.0, 12.0), fmin=2.0, fmax=100.0, K=20, n_out=96),
+    dict(fs=64.0, N=512, qs=(2.0,), fmin=3.0, fmax=32.0, K=7, norm="none", max_window_hz=2.0),
+    dict(fs=4096.0, N=6144, qs=(8.0, 40.0), fmin=30.0, fmax=1500.0, K=33),  # N/2 = 3 * 2^10
+    dict(fs=1000.0, N=3000, qs=(3.0, 30.0), fmin=5.0, fmax=490.0, K=40),    # N/2 = 1500 = 2^2 3 5^3
+]
+
+
+# ---------------------------------------------------------------------------- stages
+@pytest.mark.parametrize("N", [256, 512, 3000, 4096, 6144, 16384, 24576, 262144, 524288])
+def test_spectrum_stage(N):
+    p = make(4096.0, N, (8.0,), 30.0, 1000.0, 8)
+    B = 3
+    x = np.stack([synth.white(s, N) for s in range(B)]).astype(np.float32)
+    X = host(p.spectrum(dev(x))).astype(np.complex128)
+    for b in range(B):
+        ref = O.spectrum(x[b].astype(np.float64))
+        assert rel(X[b], ref) < 1e-6
+        assert elem_ok(X[b], ref, 1e-5)
+
+
+@pytest.mark.parametrize("i", range(len(SMALL)))
+def test_envelopes_stage_from_oracle_spectrum(i):
+    p = make(**SMALL[i])
+    g = geom_of(p)
+    x = synth.white(100 + i, g.N)
+    X = O.spectrum(x)
+    y = env_np(p, p.envelopes(dev(X.astype(np.complex64))))[0]
+    ref = np.stack([[O.forward_row(g, X, a, b) for b in range(g.K)] for a in range(g.P)])
+    assert rel(y, ref) < FWD_FROB["f32"]
+    assert elem_ok(y, ref, FWD_ELEM["f32"])
+
+
+@pytest.mark.parametrize("i", range(len(SMALL)))
+def test_accumulate_stage_from_oracle_envelopes(i):
+    p = make(**SMALL[i])
+    g = geom_of(p)
+    rng = synth.rng(7 + i)
+    Y = rng.standard_normal((g.P, g.K, g.M)) + 1j * rng.standard_normal((g.P, g.K, g.M))
+    A = host(p.accumulate(dev(Y[None].astype(np.complex64)))).astype(np.complex128)[0]
+    ref = O.accumulate(g, Y)
+    assert rel(A, ref) < 1e-6
+    assert elem_ok(A, ref, 1e-5)
+
+
+@pytest.mark.parametrize("i", range(len(SMALL)))
+def test_synthesize_stage_from_oracle_accumulator(i):
+    p = make(**SMALL[i])
+    g = geom_of(p)
+    Y = O.forward(g, synth.white(40 + i, g.N))
+    A = O.accumulate(g, Y)
+    x = host(p.synthesize(dev(A[None].astype(np.complex64))))[0].astype(np.float64)
+    ref = O.inverse(g, Y, tau=p.info["p_floor_rel"])
+    assert rel(x, ref) < 1e-5
+
+
+# ---------------------------------------------------------------------------- whole path
+@pytest.mark.parametrize("i", range(len(SMALL)))
+def test_forward_and_roundtrip_small(i):
+    p = make(**SMALL[i])
+    g = geom_of(p)
+    B = 3
+    x = np.stack([synth.white(200 + 10 * i + b, g.N) for b in range(B)]).astype(np.float32)
+    y = p.forward(dev(x))
+    Yg = env_np(p, y)
+    xh = host(p.inverse(y)).astype(np.float64)
+    tau = p.info["p_floor_rel"]
+    for b in range(B):
+        xb = x[b].astype(np.float64)
+        ref = O.forward(g, xb)
+        assert rel(Yg[b], ref) < FWD_FROB["f32"]
+        assert elem_ok(Yg[b], ref, FWD_ELEM["f32"])
+        assert rel(xh[b], O.projection(g, xb, tau=tau)) < RT["f32"]
+
+
+def test_batch_zero_is_noop():
+    p = make(**SMALL[0])
+    x = torch.zeros((0, p.N), dtype=torch.float32, device="cuda")
+    y = p.forward(x)
+    assert y.shape[0] == 0
+    assert p.inverse(y).shape == (0, p.N)
+
+
+def test_config1_float64_roundtrip():
+    """4 s at 4096 Hz, white noise + sine-Gaussian, Q=8, 64 rows 20-1024 Hz, FP64."""
+    p = make(4096.0, 16384, (8.0,), 20.0, 1024.0, 64, compute="f64")
+    g = geom_of(p)
+    x = synth.white_sine_gaussian_segment(0).astype(np.float64)
+    y = p.forward(dev(x[None]))
+    Y = env_np(p, y)[0]
+    ref = O.forward(g, x)
+    assert rel(Y, ref) < FWD_FROB["f64"]
+    assert elem_ok(Y, ref, FWD_ELEM["f64"])
+    xh = host(p.inverse(y))[0]
+    assert rel(xh, O.projection(g, x)) < RT["f64"]
+    assert p.info["p_floor_rel"] == 0.0
+
+
+@pytest.fixture(scope="module")
+def cfg2():
+    """64 s at 4096 Hz, Q in {4,8,16,32,64}, 128 rows 20-2048 Hz, FP32, coloured+whitened noise + chirp."""
+    p = make(4096.0, 262144, (4.0, 8.0, 16.0, 32.0, 64.0), 20.0, 2048.0, 128)
+    g = geom_of(p)
+    x = np.stack([synth.coloured_chirp_segment(s) for s in range(2)])
+    return p, g, x
+
+
+def test_config2_forward_sampled_rows(cfg2):
+    p, g, x = cfg2
+    y = p.forward(dev(x))
+    Y = env_np(p, y)
+    rows = [(0, 0), (0, 127), (1, 64), (2, 5), (3, 100), (4, 127), (4, 0), (2, 126)]
+    for b in range(x.shape[0]):
+        X = O.spectrum(x[b].astype(np.float64))
+        big = max(np.max(np.abs(O.forward_row(g, X, a, k))) for a, k in rows)
+        for a, k in rows:
+            ref = O.forward_row(g, X, a, k)
+            assert rel(Y[b, a, k], ref) < FWD_FROB["f32"], (a, k)
+            assert np.max(np.abs(Y[b, a, k] - ref)) <= FWD_ELEM["f32"] * big
+
+
+def test_config2_roundtrip(cfg2):
+    p, g, x = cfg2
+    xh = host(p.inverse(p.forward(dev(x)))).astype(np.float64)
+    tau = p.info["p_floor_rel"]
+    for b in range(x.shape[0]):
+        xp = O.projection(g, x[b].astype(np.float64), tau=tau)
+        assert rel(xh[b], xp) < RT["f32"]
+
+
+def test_config2_energy_identity(cfg2):
+    """sum |Y|^2 = (1/N) sum_f P[f] |X[f]|^2 at full size (App. C frame operator)."""
+    p, g, x = cfg2
+    Y = env_np(p, p.forward(dev(x[:1])))[0]
+    X = O.spectrum(x[0].astype(np.float64))
+    Pf = p.frame_operator(0)
+    assert np.sum(np.abs(Y) ** 2) == pytest.approx(np.sum(Pf * np.abs(X) ** 2) / g.N, rel=1e-5)
+
+
+def test_linearity_and_shift_invariance_gpu():
+    N = 16384
+    p = make(4096.0, N, (8.0, 16.0), 20.0, 1024.0, 48, n_out=512)
+    x1, x2 = synth.white(1, N), synth.white(2, N)
+    a, b = 0.5, -1.75
+    xs = np.stack([x1, x2, a * x1 + b * x2, np.roll(x1, N // 512)]).astype(np.float32)
+    Y = env_np(p, p.forward(dev(xs)))
+    lhs, rhs = Y[2], a * Y[0] + b * Y[1]
+    assert rel(lhs, rhs) < 2e-6
+    ph = np.exp(-2j * np.pi * p.geometry.kc / p.M)[..., None]
+    assert rel(Y[3], ph * np.roll(Y[0], 1, axis=-1)) < 2e-6
+
+
+def test_masked_and_plane_inverse():
+    p = make(**SMALL[0])
+    g = geom_of(p)
+    x = synth.white(77, g.N).astype(np.float32)
+    y = p.forward(dev(x[None]))
+    Y = env_np(p, y)[0]
+    tau = p.info["p_floor_rel"]
+    ym = y.clone()
+    ym[0, 0, 2:5] = 0
+    ym[0, 1, 7] = 0
+    Ym = Y.copy()
+    Ym[0, 2:5] = 0
+    Ym[1, 7] = 0
+    xm = host(p.inverse(ym))[0]
+    assert rel(xm, O.inverse(g, Ym, tau=tau)) < RT["f32"]
+    x1 = host(p.inverse(y, plane_mask=0b10))[0]
+    assert rel(x1, O.inverse(g, Y, planes=[1], tau=tau)) < RT["f32"]
+
+
+@pytest.mark.parametrize("env,tol_f,tol_rt", [("bf16", 1e-2, 1e-2), ("f16", 2e-3, 2e-3)])
+def test_16bit_envelopes(env, tol_f, tol_rt):
+    p = make(4096.0, 32768, (8.0, 16.0, 32.0), 20.0, 2048.0, 128, envelope=env)
+    g = geom_of(p)
+    x = synth.glitchy_segment(3, 32768, 4096.0, chirp=True)
+    y = p.forward(dev(x[None]))
+    Y = env_np(p, y)[0]
+    xd = x.astype(np.float64)
+    assert rel(Y, O.forward(g, xd)) < tol_f
+    xh = host(p.inverse(y))[0]
+    assert rel(xh, O.projection(g, xd, tau=p.info["p_floor_rel"])) < tol_rt
+
+
+def test_roundtrip_host_entry():
+    p = make(**SMALL[4])
+    g = geom_of(p)
+    B = 2
+    x = np.stack([synth.white(300 + b, g.N) for b in range(B)]).astype(np.float32)
+    xh_pinned = torch.empty((B, g.N), dtype=torch.float32).pin_memory()
+    x_pinned = torch.from_numpy(x).pin_memory()
+    x_dev = torch.empty((B, g.N), dtype=torch.float32, device="cuda")
+    xh_dev = torch.empty_like(x_dev)
+    y_dev = p.envelope_tensor(B)
+    ws, wsb = p.workspace(B)
+    qtam.qtam_roundtrip_host(p.handle, x_pinned, B, 0, xh_pinned, x_dev, y_dev, xh_dev, ws, wsb)
+    xh = xh_pinned.numpy().astype(np.float64)
+    for b in range(B):
+        assert rel(xh[b], O.projection(g, x[b].astype(np.float64), tau=p.info["p_floor_rel"])) < RT["f32"]
+
+
+def test_device_errors_are_reported():
+    p = make(**SMALL[0])
+    with pytest.raises(qtam.QtamError) as e:
+        qtam.qtam_forward(p.handle, 0, 1, 0, 0, 0)
+    assert e.value.status == 1
+    ws, wsb = p.workspace(4)
+    x = torch.zeros((4, p.N), dtype=torch.float32, device="cuda")
+    y = p.envelope_tensor(4)
+    with pytest.raises(qtam.QtamError) as e:
+        qtam.qtam_forward(p.handle, x, 4, y, ws, 16)
+    assert e.value.status == 9
