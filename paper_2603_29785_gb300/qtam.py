@@ -230,6 +230,18 @@ def qtam_status_string(status: int) -> str:
     return lib().qtam_status_string(int(status)).decode()
 
 
+def _require(t, shape, dtypes, device, name):
+    """Reject a tensor whose shape, dtype, device or layout does not match
+    what the C entry point will read or write (the ABI sees raw pointers)."""
+    ok = (hasattr(t, "is_cuda") and t.is_cuda and t.device.index == device and t.dtype in dtypes
+          and t.is_contiguous() and t.dim() == len(shape)
+          and all(s is None or int(d) == s for d, s in zip(t.shape, shape)))
+    if not ok:
+        want = "[" + ", ".join("batch" if s is None else str(s) for s in shape) + "]"
+        got = (tuple(t.shape), getattr(t, "dtype", None), getattr(t, "device", None)) if hasattr(t, "shape") else type(t)
+        raise ValueError(f"{name} must be a contiguous cuda:{device} tensor {want} of {dtypes}; got {got}")
+
+
 # ----------------------------------------------------------------------------
 # convenience wrapper
 # ----------------------------------------------------------------------------
@@ -305,25 +317,46 @@ class Plan:
     def _check_x(self, x):
         if x.dim() == 1:
             x = x.unsqueeze(0)
-        if x.dtype != self.real_dtype() or not x.is_cuda or not x.is_contiguous() or x.shape[-1] != self.N:
-            raise ValueError(f"x must be a contiguous CUDA {self.real_dtype()} tensor [batch, {self.N}]")
+        _require(x, (None, self.N), (self.real_dtype(),), self.device, "x")
         return x
+
+    def complex_dtype(self):
+        import torch
+        return torch.complex128 if self.compute == "f64" else torch.complex64
+
+    def _check_y(self, y):
+        import torch
+        if self.envelope in ("bf16", "f16"):
+            dt = torch.bfloat16 if self.envelope == "bf16" else torch.float16
+            _require(y, (None, self.P, self.K, self.M, 2), (dt,), self.device, "y")
+        else:
+            _require(y, (None, self.P, self.K, self.M), (self.complex_dtype(),), self.device, "y")
+        return y
+
+    def _check_spec(self, X, name):
+        _require(X, (None, self.Nr), (self.complex_dtype(),), self.device, name)
+        return X
 
     # -- transforms ---------------------------------------------------------
     def forward(self, x, y=None, stream=None):
         x = self._check_x(x)
         B = x.shape[0]
-        y = self.envelope_tensor(B) if y is None else y
+        y = self.envelope_tensor(B) if y is None else self._check_y(y)
+        if y.shape[0] != B:
+            raise ValueError("x and y batch sizes differ")
         ws, wsb = self.workspace(B)
         qtam_forward(self.handle, x, B, y, ws, wsb, stream)
         return y
 
     def inverse(self, y, plane_mask: int = 0, x=None, stream=None):
         import torch
+        self._check_y(y)
         B = y.shape[0]
-        x = torch.empty((B, self.N), dtype=self.real_dtype(), device=y.device) if x is None else x
+        x = torch.empty((B, self.N), dtype=self.real_dtype(), device=y.device) if x is None else self._check_x(x)
+        if x.shape[0] != B:
+            raise ValueError("x and y batch sizes differ")
         ws, wsb = self.workspace(B)
-        qtam_inverse(self.handle, y.contiguous(), B, plane_mask, x, ws, wsb, stream)
+        qtam_inverse(self.handle, y, B, plane_mask, x, ws, wsb, stream)
         return x
 
     def spectrum(self, x, stream=None):
@@ -337,25 +370,27 @@ class Plan:
         return X
 
     def envelopes(self, X, stream=None):
+        self._check_spec(X, "X")
         B = X.shape[0]
         y = self.envelope_tensor(B)
-        qtam_stage_envelopes(self.handle, X.contiguous(), B, y, stream)
+        qtam_stage_envelopes(self.handle, X, B, y, stream)
         return y
 
     def accumulate(self, y, plane_mask: int = 0, stream=None):
         import torch
+        self._check_y(y)
         B = y.shape[0]
-        cdt = torch.complex128 if self.compute == "f64" else torch.complex64
-        A = torch.empty((B, self.Nr), dtype=cdt, device=y.device)
-        qtam_stage_accumulate(self.handle, y.contiguous(), B, plane_mask, A, stream)
+        A = torch.empty((B, self.Nr), dtype=self.complex_dtype(), device=y.device)
+        qtam_stage_accumulate(self.handle, y, B, plane_mask, A, stream)
         return A
 
     def synthesize(self, A, plane_mask: int = 0, stream=None):
         import torch
+        self._check_spec(A, "A")
         B = A.shape[0]
         x = torch.empty((B, self.N), dtype=self.real_dtype(), device=A.device)
         ws, wsb = self.workspace(B)
-        qtam_stage_synthesize(self.handle, A.contiguous(), B, plane_mask, x, ws, wsb, stream)
+        qtam_stage_synthesize(self.handle, A, B, plane_mask, x, ws, wsb, stream)
         return x
 
 

@@ -109,3 +109,18 @@ def test_f64_defaults():
     assert p.info["p_floor_rel"] == 0.0 and p.info["envelope_bytes_per_segment"] == 64 * 250 * 16
     g = O.geometry(4096, 16384, (8,), 20, 1024, 64)
     assert p.info["kept_bins"] == int((O.frame_operator(g) > 0).sum())
+
+
+def test_binding_rejects_mismatched_tensors():
+    """The ABI sees raw pointers, so the binding checks every tensor's shape,
+    dtype, device and layout before a call."""
+    torch = pytest.importorskip("torch")
+    p = qtam.Plan(64.0, 512, (4.0, 8.0), 3.0, 30.0, 12, device=-1)
+    with pytest.raises(ValueError):
+        p.envelopes(torch.zeros(p.Nr, dtype=torch.complex64))            # 1-D, CPU
+    with pytest.raises(ValueError):
+        p.forward(torch.zeros((2, p.N), dtype=torch.float32))             # CPU tensor
+    with pytest.raises(ValueError):
+        p.inverse(torch.zeros((1, p.P, p.K, p.M + 1), dtype=torch.complex64))
+    with pytest.raises(ValueError):
+        p.synthesize(torch.zeros((1, p.Nr), dtype=torch.complex128))
