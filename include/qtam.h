@@ -172,6 +172,19 @@ QTAM_API qtam_status qtam_roundtrip_host(qtam_plan_t plan, const void* x_host, i
                                 void* xhat_host, void* x_dev, void* y_dev, void* xhat_dev,
                                 void* workspace, size_t workspace_bytes, void* stream);
 
+/* qtam_forward without a workspace argument, for callers that cannot
+ * allocate device memory at call time (real-time loops, host callbacks where
+ * a cudaMalloc would stall, plug-ins whose host application owns all device
+ * memory).  The paper has no counterpart: this is a library convenience.
+ * The long-FFT scratch lives in a fixed 32 MiB array inside the library,
+ * reserved on every GPU that loads it until the process exits; a batch whose
+ * qtam_workspace_size exceeds 32 MiB returns QTAM_ERR_WORKSPACE.  The call
+ * itself allocates nothing.  All calls on a device share that array: calls
+ * whose kernels may overlap on the GPU (unordered streams) race and must be
+ * serialised by the caller.  The first call on each device looks up the
+ * array's address; make it before any stream capture. */
+QTAM_API qtam_status qtam_forward_noalloc(qtam_plan_t plan, const void* x, int64_t batch, void* y, void* stream);
+
 /* Release the plan's device tables and the plan.  NULL is a no-op. */
 QTAM_API qtam_status qtam_destroy(qtam_plan_t plan);
 

@@ -412,6 +412,11 @@ qtam_status get_mask(qtam_plan_s* pl, uint64_t mask, MaskEntry** me) {
 
 }  // namespace
 
+namespace qtam {
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+int plan_device(const qtam_plan_s* plan) { return plan ? plan->device : -1; }
+}  // namespace qtam
+
 extern "C" {
 
 void qtam_plan_desc_init(qtam_plan_desc* d) {

@@ -4,7 +4,11 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "fft_core.cuh"
+
+struct qtam_plan_s;
 
 namespace qtam {
 
@@ -64,5 +68,9 @@ template <typename T>
 cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const int* row_list, int n_sel, int n_rows,
                                 int64_t Nr, const void* y, int env, cplx<T>* A, int64_t B, const cplx<T>* twM,
                                 cudaStream_t st);
+
+// ---- host helpers (qtam_api.cu) ----
+void set_last_error(const std::string& msg);   // message for qtam_last_error()
+int plan_device(const qtam_plan_s* plan);      // device of a plan, -1 when host-only
 
 }  // namespace qtam

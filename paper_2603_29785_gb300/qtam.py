@@ -78,6 +78,7 @@ SIGNATURES = {
     "qtam_stage_accumulate": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P]),
     "qtam_stage_synthesize": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P, _SZ, _P]),
     "qtam_roundtrip_host": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "qtam_forward_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
     "qtam_destroy": (ctypes.c_int, [_P]),
     "qtam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qtam_last_error": (ctypes.c_char_p, []),
@@ -219,6 +220,12 @@ def qtam_roundtrip_host(plan, x_host, batch, plane_mask, xhat_host, x_dev, y_dev
     _check(lib().qtam_roundtrip_host(plan, _ptr(x_host), int(batch), int(plane_mask), _ptr(xhat_host), _ptr(x_dev),
                                      _ptr(y_dev), _ptr(xhat_dev), _ptr(workspace), int(workspace_bytes),
                                      _stream(stream)))
+
+
+def qtam_forward_noalloc(plan, x, batch, y, stream=None):
+    """qtam_forward with the library's fixed scratch array instead of a
+    caller workspace (for callers that cannot allocate at call time)."""
+    _check(lib().qtam_forward_noalloc(plan, _ptr(x), int(batch), _ptr(y), _stream(stream)))
 
 
 def qtam_destroy(plan):
