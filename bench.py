@@ -36,12 +36,14 @@ WORKLOAD_NAME = "64 s @ 4096 Hz segments, Q {4,8,16,32,64} x 128 log rows 20-204
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--batch", type=int, default=64, help="segments per GPU per step")
     ap.add_argument("--impl", default="qtam", choices=["qtam", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-segments", type=int, default=4)
+    ap.add_argument("--variant", type=int, default=None,
+                    help="row-kernel variant id (default: chosen by the autotuner)")
     return ap.parse_args()
 
 
@@ -72,7 +74,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
@@ -178,6 +180,12 @@ def run_gpu(args, rank, world, local):
     x_host = make_inputs(seeds)
     p = qtam.Plan(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"],
                   device=local)
+    if args.variant is not None:
+        qtam.qtam_plan_set_variant(p.handle, args.variant)
+        chosen = qtam.qtam_variant_describe(args.variant)
+    else:
+        from paper_2603_29785_gb300 import tune as qtune
+        chosen = qtune.tune(p, B)
     N, Nr, M, P, K = p.N, p.Nr, p.M, p.P, p.K
     dev = f"cuda:{local}"
     x = torch.from_numpy(x_host).to(dev)
@@ -290,7 +298,8 @@ def run_gpu(args, rank, world, local):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "segments_per_gpu": B, "N": N, "M": M, "planes": P,
                    "rows_per_plane": K, "parallelism": f"replicas x{world}",
-                   "l2": "flushed between steps (256 MB write outside the timed events)"},
+                   "l2": "flushed between steps (256 MB write outside the timed events)",
+                   "row_variant": chosen["name"]},
         "roofline": roofline,
         "path_hbm_frac": round(path_frac, 4),
         "stages": kernels,

@@ -112,6 +112,7 @@ typedef struct {
   double kappa;                   /* max over kept bins of max_k W_k / P (all planes) */
   int64_t kept_bins;              /* |F_tau| for all planes */
   int64_t device_bytes;           /* bytes of resident plan tables on the device */
+  int32_t row_variant;            /* row-kernel variant in use (-1: runtime engine) */
 } qtam_plan_info_t;
 
 /* Fill *d with defaults: bisquare, L2 norm, q_width sqrt(11), automatic clamp
@@ -134,6 +135,24 @@ QTAM_API qtam_status qtam_plan_rows(qtam_plan_t plan, double* f, int64_t* kc, in
 /* Frame operator P[f], f = 0..N/2, of the planes in plane_mask (bit p =
  * plane p; 0 = all planes), FP64, into the caller's host array of N/2+1. */
 QTAM_API qtam_status qtam_frame_operator(qtam_plan_t plan, uint64_t plane_mask, double* p_out);
+
+/* Row-kernel variants (launch shapes) usable for this plan: the runtime
+ * mixed-radix engine (-1, any length) and the compile-time variants built for
+ * the plan's envelope length M (FP32 compute).  Writes up to `capacity` ids
+ * into `ids` and the total into *count.  All variants compute the same
+ * transform; they differ in radix sequence, rows per block and occupancy.
+ * An autotuner times them (qtam_stage_envelopes / qtam_stage_accumulate)
+ * and keeps the fastest with qtam_plan_set_variant. */
+QTAM_API qtam_status qtam_plan_variants(qtam_plan_t plan, int32_t* ids, int32_t capacity, int32_t* count);
+
+/* Select the row-kernel variant for subsequent calls on this plan.  Not
+ * synchronised with calls running concurrently on other threads. */
+QTAM_API qtam_status qtam_plan_set_variant(qtam_plan_t plan, int32_t variant);
+
+/* Describe a variant: a name (radices, rows per block, occupancy target)
+ * into name[capacity], threads per block and rows per block. */
+QTAM_API qtam_status qtam_variant_describe(int32_t variant, char* name, size_t capacity, int32_t* threads,
+                                           int32_t* rows_per_block);
 
 /* Bytes of device workspace one qtam_forward/qtam_inverse call on `batch`
  * segments needs (the long-FFT buffers and the spectrum accumulator). */

@@ -17,7 +17,6 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
-#include <utility>
 
 namespace qtam {
 
@@ -73,14 +72,6 @@ __host__ __device__ constexpr double ce_sin2pi(long p, long q) {
   double th = 1.5707963267948966192 * (double)rem / (double)q;
   double c = ce_cos_q(th), s = ce_sin_q(th);
   return qd == 0 ? s : qd == 1 ? c : qd == 2 ? -s : -c;
-}
-
-template <int... Is, class F>
-__device__ __forceinline__ void sfor_impl(std::integer_sequence<int, Is...>, F&& f) {
-  (f(std::integral_constant<int, Is>{}), ...);
-}
-template <int N, class F> __device__ __forceinline__ void sfor(F&& f) {
-  sfor_impl(std::make_integer_sequence<int, N>{}, f);
 }
 
 // ---------------------------------------------------------------------------
@@ -141,42 +132,92 @@ template <int S> struct Dft<5, S> {
   }
 };
 
+// Twiddles of a composite radix: w_R^e = (cos 2 pi e/R, sin 2 pi e/R) for
+// e < R, built at compile time into constant memory and read at indices that
+// are compile-time constants after unrolling (constant-bank operands).
+template <int R, typename T> struct TwTab {
+  T c[R], s[R];
+};
+template <int R, typename T> constexpr TwTab<R, T> make_twtab() {
+  TwTab<R, T> t{};
+  for (int e = 0; e < R; ++e) {
+    t.c[e] = (T)ce_cos2pi(e, R);
+    t.s[e] = (T)ce_sin2pi(e, R);
+  }
+  return t;
+}
+template <int R> struct TwConst;
+#define QTAM_TWCONST(R)                                                            \
+  static __constant__ TwTab<R, float> kTwF##R = make_twtab<R, float>();            \
+  static __constant__ TwTab<R, double> kTwD##R = make_twtab<R, double>();          \
+  template <> struct TwConst<R> {                                                  \
+    __device__ __forceinline__ static float2 get(int e, float) {                   \
+      return make_float2(kTwF##R.c[e], kTwF##R.s[e]);                              \
+    }                                                                              \
+    __device__ __forceinline__ static double2 get(int e, double) {                 \
+      return make_double2(kTwD##R.c[e], kTwD##R.s[e]);                             \
+    }                                                                              \
+  };
+
 // composite R = R1 * R2: index j = R2 j1 + j2, output k = k1 + R1 k2
 //   b[j2][k1] = DFT_R1 over j1 of a[R2 j1 + j2];  b *= w_R^(S j2 k1);
 //   y[k1 + R1 k2] = DFT_R2 over j2 of b[j2][k1]
+// Plain unrolled loops: every array index is a compile-time constant, so the
+// arrays stay in registers.
 template <int R1, int R2, int S> struct DftComposite {
   template <typename V> __device__ __forceinline__ static void run(V* a) {
     using T = decltype(V::x);
     constexpr int R = R1 * R2;
     V b[R];
-    sfor<R2>([&](auto J2) {
-      constexpr int j2 = decltype(J2)::value;
+#pragma unroll
+    for (int j2 = 0; j2 < R2; ++j2) {
       V col[R1];
-      sfor<R1>([&](auto J1) { constexpr int j1 = decltype(J1)::value; col[j1] = a[R2 * j1 + j2]; });
+#pragma unroll
+      for (int j1 = 0; j1 < R1; ++j1) col[j1] = a[R2 * j1 + j2];
       Dft<R1, S>::run(col);
-      sfor<R1>([&](auto K1) {
-        constexpr int k1 = decltype(K1)::value;
-        constexpr int e = (j2 * k1) % R;
-        if constexpr (e == 0) {
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) {
+        const int e = (j2 * k1) % R;
+        if (e == 0) {
           b[j2 * R1 + k1] = col[k1];
         } else {
-          constexpr T c = (T)ce_cos2pi(e, R);
-          constexpr T s = (T)(S * ce_sin2pi(e, R));
-          b[j2 * R1 + k1] = cmul(col[k1], mk<V>(c, s));
+          V w = TwConst<R>::get(e, T());
+          if (S < 0) w.y = -w.y;
+          b[j2 * R1 + k1] = cmul(col[k1], w);
         }
-      });
-    });
-    sfor<R1>([&](auto K1) {
-      constexpr int k1 = decltype(K1)::value;
+      }
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
       V row[R2];
-      sfor<R2>([&](auto J2) { constexpr int j2 = decltype(J2)::value; row[j2] = b[j2 * R1 + k1]; });
+#pragma unroll
+      for (int j2 = 0; j2 < R2; ++j2) row[j2] = b[j2 * R1 + k1];
       Dft<R2, S>::run(row);
-      sfor<R2>([&](auto K2) { constexpr int k2 = decltype(K2)::value; a[k1 + R1 * k2] = row[k2]; });
-    });
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) a[k1 + R1 * k2] = row[k2];
+    }
   }
 };
+QTAM_TWCONST(6)
+QTAM_TWCONST(8)
+QTAM_TWCONST(9)
+QTAM_TWCONST(10)
+QTAM_TWCONST(12)
+QTAM_TWCONST(15)
+QTAM_TWCONST(16)
+QTAM_TWCONST(20)
+QTAM_TWCONST(25)
+QTAM_TWCONST(32)
+template <int S> struct Dft<6, S> : DftComposite<2, 3, S> {};
 template <int S> struct Dft<8, S> : DftComposite<2, 4, S> {};
+template <int S> struct Dft<9, S> : DftComposite<3, 3, S> {};
+template <int S> struct Dft<10, S> : DftComposite<2, 5, S> {};
+template <int S> struct Dft<12, S> : DftComposite<4, 3, S> {};
+template <int S> struct Dft<15, S> : DftComposite<3, 5, S> {};
 template <int S> struct Dft<16, S> : DftComposite<4, 4, S> {};
+template <int S> struct Dft<20, S> : DftComposite<4, 5, S> {};
+template <int S> struct Dft<25, S> : DftComposite<5, 5, S> {};
+template <int S> struct Dft<32, S> : DftComposite<4, 8, S> {};
 
 // items held in registers per thread for one stage of radix R (~16 complex)
 __host__ __device__ constexpr int ipt_for(int R) {

@@ -12,11 +12,38 @@
 // inverse (with X_hat = A / P read through the plan's 1/P table and the DC
 // and Nyquist bins taken real) feeds the row pass, then the column pass
 // writes x_hat[2m] + i x_hat[2m+1] directly.
+#include "fft_static.cuh"
 #include "qtam_internal.h"
 
 namespace qtam {
 
 namespace {
+
+// FFT engines for the four-step passes: the runtime engine takes any
+// 2^a 3^b 5^c length and interleave count; the static engines fix both.
+struct GenLong {
+  RadixPlan rp;
+  int nbs;
+  static constexpr int NT = kMaxBlock;
+  static constexpr int MINB = 1;
+  __device__ __forceinline__ int m() const { return rp.m; }
+  __device__ __forceinline__ int nb_shift() const { return nbs; }
+  template <int S, typename V, class L, class St>
+  __device__ __forceinline__ void run(V* sm, const V* tw, int twstride, const L& ld, const St& st) const {
+    block_fft<S>(rp, nbs, sm, tw, twstride, ld, st);
+  }
+};
+template <int M_, int NBS_, int... Rs> struct StatLong {
+  static constexpr int NT = StaticThreads<M_, NBS_, Rs...>::value;
+  static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;   // at least 512 threads per SM
+  __device__ __forceinline__ int m() const { return M_; }
+  __device__ __forceinline__ int nb_shift() const { return NBS_; }
+  template <int S, typename V, class L, class St>
+  __device__ __forceinline__ void run(V* sm, const V* tw, int twstride, const L& ld, const St& st) const {
+    StaticFFT<S, M_, NT, NBS_, Rs...>::run(sm, tw, twstride, ld, st);
+  }
+  static size_t smem_bytes(size_t elem) { return StaticFFT<1, M_, NT, NBS_, Rs...>::smem_elems() * elem; }
+};
 
 template <typename V> struct LoadColumns {
   const V* zs; int n2; int c0;
@@ -38,30 +65,30 @@ template <typename V> struct StoreRowsTransposed {
   __device__ __forceinline__ void put(int b, int k2, V v) const { Zs[(int64_t)k2 * n1 + r0 + b] = v; }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kMaxBlock) k_col_forward(RadixPlan rp, int n, int n2, int nbs, const cplx<T>* __restrict__ z,
-                                                      cplx<T>* __restrict__ U, const cplx<T>* __restrict__ twn) {
+template <class Eng, typename T>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_col_forward(Eng eng, int n, int n2, const cplx<T>* __restrict__ z,
+                                                          cplx<T>* __restrict__ U, const cplx<T>* __restrict__ twn) {
   using V = cplx<T>;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int64_t seg = blockIdx.y;
-  const int c0 = blockIdx.x << nbs;
+  const int c0 = blockIdx.x << eng.nb_shift();
   LoadColumns<V> ld{z + seg * n, n2, c0};
   StoreColumnsTwiddled<V> stv{U + seg * n, twn, n2, c0};
-  block_fft<-1>(rp, nbs, sm, twn, n / rp.m, ld, stv);
+  eng.template run<-1>(sm, twn, n / eng.m(), ld, stv);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kMaxBlock) k_row_forward(RadixPlan rp, int n, int n1, int nbs, const cplx<T>* __restrict__ U,
-                                                      cplx<T>* __restrict__ Z, const cplx<T>* __restrict__ twn) {
+template <class Eng, typename T>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_row_forward(Eng eng, int n, int n1, const cplx<T>* __restrict__ U,
+                                                          cplx<T>* __restrict__ Z, const cplx<T>* __restrict__ twn) {
   using V = cplx<T>;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int64_t seg = blockIdx.y;
-  const int r0 = blockIdx.x << nbs;
-  LoadRows<V> ld{U + seg * n, rp.m, r0};
+  const int r0 = blockIdx.x << eng.nb_shift();
+  LoadRows<V> ld{U + seg * n, eng.m(), r0};
   StoreRowsTransposed<V> stv{Z + seg * n, n1, r0};
-  block_fft<-1>(rp, nbs, sm, twn, n / rp.m, ld, stv);
+  eng.template run<-1>(sm, twn, n / eng.m(), ld, stv);
 }
 
 // w_N^k for k in [0, n]: table holds k <= n/2; w_N^(n-k) = -conj(w_N^k)
@@ -129,35 +156,73 @@ template <typename V> struct StoreColumns {
   __device__ __forceinline__ void put(int b, int m1, V v) const { xs[(int64_t)m1 * n2 + c0 + b] = v; }
 };
 
-template <typename T>
-__global__ void __launch_bounds__(kMaxBlock) k_row_inverse(RadixPlan rp, int n, int n1, int nbs, const cplx<T>* __restrict__ A,
-                                                      const T* __restrict__ invP, cplx<T>* __restrict__ Vb,
-                                                      const cplx<T>* __restrict__ twn, const cplx<T>* __restrict__ twN,
-                                                      T scale) {
+template <class Eng, typename T>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_row_inverse(Eng eng, int n, int n1, const cplx<T>* __restrict__ A,
+                                                          const T* __restrict__ invP, cplx<T>* __restrict__ Vb,
+                                                          const cplx<T>* __restrict__ twn,
+                                                          const cplx<T>* __restrict__ twN, T scale) {
   using V = cplx<T>;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int64_t seg = blockIdx.y;
-  const int r0 = blockIdx.x << nbs;
+  const int r0 = blockIdx.x << eng.nb_shift();
   LoadUntangleInverse<T> ld{A + seg * (int64_t)(n + 1), invP, twN, n, n1, r0, scale};
-  StoreRowsTwiddledConj<V> stv{Vb + seg * n, twn, rp.m, r0};
-  block_fft<+1>(rp, nbs, sm, twn, n / rp.m, ld, stv);
+  StoreRowsTwiddledConj<V> stv{Vb + seg * n, twn, eng.m(), r0};
+  eng.template run<+1>(sm, twn, n / eng.m(), ld, stv);
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kMaxBlock) k_col_inverse(RadixPlan rp, int n, int n2, int nbs, const cplx<T>* __restrict__ Vb,
-                                                      cplx<T>* __restrict__ xout, const cplx<T>* __restrict__ twn) {
+template <class Eng, typename T>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_col_inverse(Eng eng, int n, int n2, const cplx<T>* __restrict__ Vb,
+                                                          cplx<T>* __restrict__ xout, const cplx<T>* __restrict__ twn) {
   using V = cplx<T>;
-  extern __shared__ unsigned char smraw[];
+  extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int64_t seg = blockIdx.y;
-  const int c0 = blockIdx.x << nbs;
+  const int c0 = blockIdx.x << eng.nb_shift();
   LoadColumns<V> ld{Vb + seg * n, n2, c0};
   StoreColumns<V> stv{xout + seg * n, n2, c0};
-  block_fft<+1>(rp, nbs, sm, twn, n / rp.m, ld, stv);
+  eng.template run<+1>(sm, twn, n / eng.m(), ld, stv);
 }
 
 constexpr int64_t kMaxGridY = 65535;
+
+// Static engines for power-of-two sub-lengths (FP32): column passes
+// interleave 16 columns, row passes 4 rows.
+#define QTAM_LONG_CASES(X, NBS)      \
+  X(32, NBS, 8, 4)                   \
+  X(64, NBS, 16, 4)                  \
+  X(128, NBS, 16, 8)                 \
+  X(256, NBS, 16, 16)                \
+  X(512, NBS, 16, 32)                \
+  X(1024, NBS, 32, 32)
+
+template <class Eng, class K, class... Args>
+void launch_pass(K kernel, const Eng& eng, size_t smem, dim3 g, cudaStream_t st, Args... args) {
+  allow_smem((const void*)kernel, smem);
+  kernel<<<g, Eng::NT, smem, st>>>(eng, args...);
+}
+
+// Call f(engine, smem) with the static engine for (m, nbs) when one exists
+// (FP32), else with the runtime engine.
+#define QTAM_CASE(M, NBS, ...)                   \
+  case M: {                                      \
+    using E = StatLong<M, NBS, __VA_ARGS__>;     \
+    f(E(), E::smem_bytes(sizeof(float2)));       \
+    return;                                      \
+  }
+
+template <typename T, class F>
+void with_engine(const RadixPlan& rp, int nbs, int static_nbs, size_t gen_smem, F&& f) {
+  if constexpr (sizeof(T) == 4) {
+    if (nbs == static_nbs && static_nbs == 4) {
+      switch (rp.m) { QTAM_LONG_CASES(QTAM_CASE, 4) default: break; }
+    } else if (nbs == static_nbs && static_nbs == 2) {
+      switch (rp.m) { QTAM_LONG_CASES(QTAM_CASE, 2) default: break; }
+    }
+  }
+  f(GenLong{rp, nbs}, gen_smem);
+}
+#undef QTAM_CASE
 
 }  // namespace
 
@@ -167,12 +232,16 @@ cudaError_t launch_spectrum(const LongCfg& c, const cplx<T>* z, cplx<T>* U, cplx
   for (int64_t s0 = 0; s0 < B; s0 += kMaxGridY) {
     const int64_t nb = (B - s0) < kMaxGridY ? (B - s0) : kMaxGridY;
     const int64_t off = s0 * c.n;
-    dim3 g1(c.n2 >> c.col_nbs, (unsigned)nb);
-    allow_smem((const void*)k_col_forward<T>, c.col_smem);
-    k_col_forward<T><<<g1, c.col_threads, c.col_smem, st>>>(c.rp1, c.n, c.n2, c.col_nbs, z + off, U + off, twn);
-    dim3 g2(c.n1 >> c.row_nbs, (unsigned)nb);
-    allow_smem((const void*)k_row_forward<T>, c.row_smem);
-    k_row_forward<T><<<g2, c.row_threads, c.row_smem, st>>>(c.rp2, c.n, c.n1, c.row_nbs, U + off, Z + off, twn);
+    with_engine<T>(c.rp1, c.col_nbs, 4, c.col_smem, [&](auto eng, size_t smem) {
+      using E = decltype(eng);
+      dim3 g(c.n2 >> c.col_nbs, (unsigned)nb);
+      launch_pass(k_col_forward<E, T>, eng, smem, g, st, c.n, c.n2, z + off, U + off, twn);
+    });
+    with_engine<T>(c.rp2, c.row_nbs, 2, c.row_smem, [&](auto eng, size_t smem) {
+      using E = decltype(eng);
+      dim3 g(c.n1 >> c.row_nbs, (unsigned)nb);
+      launch_pass(k_row_forward<E, T>, eng, smem, g, st, c.n, c.n1, (const cplx<T>*)(U + off), Z + off, twn);
+    });
     dim3 g3((unsigned)((c.n / 2 + 1 + 255) / 256), (unsigned)nb);
     k_untangle_forward<T><<<g3, 256, 0, st>>>(c.n, Z + off, X + s0 * (int64_t)(c.n + 1), twN);
   }
@@ -185,13 +254,17 @@ cudaError_t launch_synthesis(const LongCfg& c, const cplx<T>* A, const T* invP, 
   for (int64_t s0 = 0; s0 < B; s0 += kMaxGridY) {
     const int64_t nb = (B - s0) < kMaxGridY ? (B - s0) : kMaxGridY;
     const int64_t off = s0 * c.n;
-    dim3 g2(c.n1 >> c.row_nbs, (unsigned)nb);
-    allow_smem((const void*)k_row_inverse<T>, c.row_smem);
-    k_row_inverse<T><<<g2, c.row_threads, c.row_smem, st>>>(c.rp2, c.n, c.n1, c.row_nbs, A + s0 * (int64_t)(c.n + 1),
-                                                            invP, Vb + off, twn, twN, (T)1 / (T)c.n);
-    dim3 g1(c.n2 >> c.col_nbs, (unsigned)nb);
-    allow_smem((const void*)k_col_inverse<T>, c.col_smem);
-    k_col_inverse<T><<<g1, c.col_threads, c.col_smem, st>>>(c.rp1, c.n, c.n2, c.col_nbs, Vb + off, xout + off, twn);
+    with_engine<T>(c.rp2, c.row_nbs, 2, c.row_smem, [&](auto eng, size_t smem) {
+      using E = decltype(eng);
+      dim3 g(c.n1 >> c.row_nbs, (unsigned)nb);
+      launch_pass(k_row_inverse<E, T>, eng, smem, g, st, c.n, c.n1, A + s0 * (int64_t)(c.n + 1), invP, Vb + off,
+                  twn, twN, (T)1 / (T)c.n);
+    });
+    with_engine<T>(c.rp1, c.col_nbs, 4, c.col_smem, [&](auto eng, size_t smem) {
+      using E = decltype(eng);
+      dim3 g(c.n2 >> c.col_nbs, (unsigned)nb);
+      launch_pass(k_col_inverse<E, T>, eng, smem, g, st, c.n, c.n2, (const cplx<T>*)(Vb + off), xout + off, twn);
+    });
   }
   return cudaGetLastError();
 }

@@ -1,5 +1,5 @@
-// Per-row kernels of the QTAM transform pair: one thread block per
-// (segment, plane/row) window.
+// Per-row kernels of the QTAM transform pair: each thread block transforms
+// 2^NBS (segment, plane/row) windows.
 //
 // Forward (steps a2-a4; Sec. III demodulation, App. A): the first FFT stage
 // gathers the row's band straight from the L2-resident spectrum, applies the
@@ -14,9 +14,13 @@
 // memory, and the last stage keeps only the band offsets |d| <= h, re-scales
 // by sqrt(N/M), weights by c_k W'(d) and adds the result into the spectrum
 // accumulator A[k_c + d] with vector atomics (A stays L2-resident).
+//
+// The FFT itself is either the runtime engine (any 2^a 3^b 5^c length) or a
+// compile-time engine registered below for the lengths the workloads use.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include "fft_static.cuh"
 #include "qtam_internal.h"
 
 namespace qtam {
@@ -51,47 +55,48 @@ template <> struct Env<double2, ENV_F64> {
   __device__ __forceinline__ static double2 from(S v) { return v; }
 };
 
-// band offset of baseband position i (i = d mod M), or a sentinel outside the band
-__device__ __forceinline__ int band_offset(int i, int h, int M) {
-  return i <= h ? i : (i >= M - h ? i - M : INT32_MIN);
-}
+// Per-thread view of the row it works on.  Every call a thread makes uses
+// the same interleave slot b = threadIdx.x mod 2^NBS (block sizes are whole
+// warps), so the row descriptor is read once, not per element.
+template <typename T> struct RowCtx {
+  int kc, h, M, nhalf;
+  T c, inv_h2;
+  bool valid;
+  // band offset of baseband position i (i = d mod M); false outside the band
+  __device__ __forceinline__ bool offset(int i, int& d, int& f) const {
+    d = i <= h ? i : i - M;
+    f = kc + d;
+    return valid && (i <= h || i >= M - h) && f >= 0 && f <= nhalf;
+  }
+  __device__ __forceinline__ T weight(int d) const {
+    const int a = d < 0 ? -d : d;
+    return c * bisquare<T>(a, h, inv_h2);
+  }
+};
 
 template <typename T> struct LoadBand {
   using V = cplx<T>;
-  const V* Xs; int kc; int h; int M; int nhalf; T c; T inv_h2;
+  const V* Xs;
+  RowCtx<T> r;
   __device__ __forceinline__ V get(int, int i) const {
-    const int d = band_offset(i, h, M);
-    const int f = kc + d;
-    if (d == INT32_MIN || f < 0 || f > nhalf) return mk<V>((T)0, (T)0);
-    const int a = d < 0 ? -d : d;
-    return cscale(Xs[f], c * bisquare<T>(a, h, inv_h2));
+    int d, f;
+    if (!r.offset(i, d, f)) return mk<V>((T)0, (T)0);
+    return cscale(Xs[f], r.weight(d));
   }
 };
 template <typename V, int E> struct StoreEnvelope {
   typename Env<V, E>::S* ys;
-  __device__ __forceinline__ void put(int, int i, V v) const { ys[i] = Env<V, E>::to(v); }
+  bool valid;
+  __device__ __forceinline__ void put(int, int i, V v) const {
+    if (valid) ys[i] = Env<V, E>::to(v);
+  }
 };
-
-template <typename T, int E>
-__global__ void __launch_bounds__(kMaxBlock) k_rows_forward(RadixPlan rp, const RowDev<T>* __restrict__ rows, int n_rows,
-                                                       int64_t Nr, const cplx<T>* __restrict__ X,
-                                                       typename Env<cplx<T>, E>::S* __restrict__ y,
-                                                       const cplx<T>* __restrict__ twM) {
-  using V = cplx<T>;
-  extern __shared__ unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int64_t bid = blockIdx.x;
-  const int64_t seg = bid / n_rows;
-  const int row = (int)(bid - seg * n_rows);
-  const RowDev<T> rd = rows[row];
-  LoadBand<T> ld{X + seg * Nr, rd.kc, rd.h, rp.m, (int)(Nr - 1), rd.c_fwd, rd.inv_h2};
-  StoreEnvelope<V, E> stv{y + bid * rp.m};
-  block_fft<+1>(rp, 0, sm, twM, 1, ld, stv);
-}
-
 template <typename V, int E> struct LoadEnvelope {
   const typename Env<V, E>::S* ys;
-  __device__ __forceinline__ V get(int, int i) const { return Env<V, E>::from(ys[i]); }
+  bool valid;
+  __device__ __forceinline__ V get(int, int i) const {
+    return valid ? Env<V, E>::from(ys[i]) : mk<V>(0, 0);
+  }
 };
 
 template <typename V> __device__ __forceinline__ void add_to(V* p, V v);
@@ -103,61 +108,229 @@ template <> __device__ __forceinline__ void add_to<double2>(double2* p, double2 
 
 template <typename T> struct AccumulateBand {
   using V = cplx<T>;
-  V* As; int kc; int h; int M; int nhalf; T c; T inv_h2;
+  V* As;
+  RowCtx<T> r;
   __device__ __forceinline__ void put(int, int i, V v) const {
-    const int d = band_offset(i, h, M);
-    const int f = kc + d;
-    if (d == INT32_MIN || f < 0 || f > nhalf) return;
-    const int a = d < 0 ? -d : d;
-    add_to(&As[f], cscale(v, c * bisquare<T>(a, h, inv_h2)));
+    int d, f;
+    if (!r.offset(i, d, f)) return;
+    add_to(&As[f], cscale(v, r.weight(d)));
   }
 };
 
-template <typename T, int E>
-__global__ void __launch_bounds__(kMaxBlock) k_rows_inverse(RadixPlan rp, const RowDev<T>* __restrict__ rows,
-                                                       const int* __restrict__ row_list, int n_sel, int n_rows,
-                                                       int64_t Nr, const typename Env<cplx<T>, E>::S* __restrict__ y,
-                                                       cplx<T>* __restrict__ A, const cplx<T>* __restrict__ twM) {
-  using V = cplx<T>;
-  extern __shared__ unsigned char smraw[];
-  V* sm = reinterpret_cast<V*>(smraw);
-  const int64_t bid = blockIdx.x;
-  const int64_t seg = bid / n_sel;
-  const int row = row_list[bid - seg * n_sel];
-  const RowDev<T> rd = rows[row];
-  LoadEnvelope<V, E> ld{y + (seg * n_rows + row) * rp.m};
-  AccumulateBand<T> stv{A + seg * Nr, rd.kc, rd.h, rp.m, (int)(Nr - 1), rd.c_inv, rd.inv_h2};
-  block_fft<-1>(rp, 0, sm, twM, 1, ld, stv);
+// ---- FFT engines ----------------------------------------------------------
+struct GenericEngine {
+  RadixPlan rp;
+  static constexpr int NBS = 0;
+  __device__ __forceinline__ int m() const { return rp.m; }
+  template <int S, typename V, class L, class St>
+  __device__ __forceinline__ void run(V* sm, const V* tw, const L& ld, const St& st) const {
+    block_fft<S>(rp, 0, sm, tw, 1, ld, st);
+  }
+};
+
+template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
+  static constexpr int M = M_;
+  static constexpr int NBS = NBS_;
+  static constexpr int NT = StaticThreads<M_, NBS_, Rs...>::value;
+  static constexpr int MINB = MINB_;
+  __device__ __forceinline__ int m() const { return M; }
+  template <int S, typename V, class L, class St>
+  __device__ __forceinline__ void run(V* sm, const V* tw, const L& ld, const St& st) const {
+    StaticFFT<S, M, NT, NBS, Rs...>::run(sm, tw, 1, ld, st);
+  }
+  static size_t smem_bytes(size_t elem) { return StaticFFT<1, M, NT, NBS, Rs...>::smem_elems() * elem; }
+};
+
+template <typename T>
+__device__ __forceinline__ RowCtx<T> row_ctx(const RowDev<T>* rows, int row, int M, int64_t Nr, bool valid, bool inv) {
+  RowCtx<T> r;
+  if (valid) {
+    const RowDev<T> rd = rows[row];
+    r.kc = rd.kc;
+    r.h = rd.h;
+    r.c = inv ? rd.c_inv : rd.c_fwd;
+    r.inv_h2 = rd.inv_h2;
+  } else {
+    r.kc = 0; r.h = 0; r.c = 0; r.inv_h2 = 0;
+  }
+  r.M = M;
+  r.nhalf = (int)(Nr - 1);
+  r.valid = valid;
+  return r;
 }
 
+template <class Eng, typename T, int E>
+__device__ __forceinline__ void rows_forward_body(const Eng& eng, const RowDev<T>* __restrict__ rows, int n_rows,
+                                                  int64_t Nr, const cplx<T>* __restrict__ X,
+                                                  typename Env<cplx<T>, E>::S* __restrict__ y, int64_t n_units,
+                                                  const cplx<T>* __restrict__ twM) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int M = eng.m();
+  const int64_t unit = ((int64_t)blockIdx.x << Eng::NBS) + (threadIdx.x & ((1 << Eng::NBS) - 1));
+  const bool valid = unit < n_units;
+  const int64_t seg = valid ? unit / n_rows : 0;
+  const int row = valid ? (int)(unit - seg * n_rows) : 0;
+  LoadBand<T> ld{X + seg * Nr, row_ctx<T>(rows, row, M, Nr, valid, false)};
+  StoreEnvelope<V, E> stv{y + (valid ? unit : 0) * M, valid};
+  eng.template run<+1>(sm, twM, ld, stv);
+}
+
+template <class Eng, typename T, int E>
+__device__ __forceinline__ void rows_inverse_body(const Eng& eng, const RowDev<T>* __restrict__ rows,
+                                                  const int* __restrict__ row_list, int n_sel, int n_rows, int64_t Nr,
+                                                  const typename Env<cplx<T>, E>::S* __restrict__ y,
+                                                  cplx<T>* __restrict__ A, int64_t n_units,
+                                                  const cplx<T>* __restrict__ twM) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int M = eng.m();
+  const int64_t unit = ((int64_t)blockIdx.x << Eng::NBS) + (threadIdx.x & ((1 << Eng::NBS) - 1));
+  const bool valid = unit < n_units;
+  const int64_t seg = valid ? unit / n_sel : 0;
+  const int row = valid ? row_list[unit - seg * n_sel] : 0;
+  LoadEnvelope<V, E> ld{y + (seg * n_rows + row) * M, valid};
+  AccumulateBand<T> stv{A + seg * Nr, row_ctx<T>(rows, row, M, Nr, valid, true)};
+  eng.template run<-1>(sm, twM, ld, stv);
+}
+
+template <typename T, int E>
+__global__ void __launch_bounds__(kMaxBlock, 1)
+    k_rows_forward(GenericEngine eng, const RowDev<T>* __restrict__ rows, int n_rows, int64_t Nr,
+                   const cplx<T>* __restrict__ X, typename Env<cplx<T>, E>::S* __restrict__ y, int64_t n_units,
+                   const cplx<T>* __restrict__ twM) {
+  rows_forward_body<GenericEngine, T, E>(eng, rows, n_rows, Nr, X, y, n_units, twM);
+}
+template <typename T, int E>
+__global__ void __launch_bounds__(kMaxBlock, 1)
+    k_rows_inverse(GenericEngine eng, const RowDev<T>* __restrict__ rows, const int* __restrict__ row_list, int n_sel,
+                   int n_rows, int64_t Nr, const typename Env<cplx<T>, E>::S* __restrict__ y, cplx<T>* __restrict__ A,
+                   int64_t n_units, const cplx<T>* __restrict__ twM) {
+  rows_inverse_body<GenericEngine, T, E>(eng, rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM);
+}
+
+template <class Eng, int E>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB)
+    k_rows_forward_s(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
+                     typename Env<float2, E>::S* __restrict__ y, int64_t n_units, const float2* __restrict__ twM) {
+  rows_forward_body<Eng, float, E>(Eng(), rows, n_rows, Nr, X, y, n_units, twM);
+}
+template <class Eng, int E>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB)
+    k_rows_inverse_s(const RowDev<float>* __restrict__ rows, const int* __restrict__ row_list, int n_sel, int n_rows,
+                     int64_t Nr, const typename Env<float2, E>::S* __restrict__ y, float2* __restrict__ A,
+                     int64_t n_units, const float2* __restrict__ twM) {
+  rows_inverse_body<Eng, float, E>(Eng(), rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM);
+}
+
+// ---- registry of compile-time variants (FP32 compute) ------------------------
+template <class Eng, int E>
+cudaError_t fwd_launch(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
+                       const float2* twM, cudaStream_t st) {
+  const int64_t units = B * n_rows;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_forward_s<Eng, E>, smem);
+  k_rows_forward_s<Eng, E><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, n_rows, Nr, X, static_cast<typename Env<float2, E>::S*>(y), units, twM);
+  return cudaGetLastError();
+}
+template <class Eng, int E>
+cudaError_t inv_launch(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
+                       const void* y, float2* A, int64_t B, const float2* twM, cudaStream_t st) {
+  const int64_t units = B * n_sel;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_inverse_s<Eng, E>, smem);
+  k_rows_inverse_s<Eng, E><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, row_list, n_sel, n_rows, Nr, static_cast<const typename Env<float2, E>::S*>(y), A, units, twM);
+  return cudaGetLastError();
+}
+
+template <class Eng> RowVariant make_variant(const char* name) {
+  RowVariant v;
+  v.M = Eng::M;
+  v.rows_per_block = 1 << Eng::NBS;
+  v.threads = Eng::NT;
+  v.smem = Eng::smem_bytes(sizeof(float2));
+  v.name = name;
+  v.fwd[ENV_F32] = fwd_launch<Eng, ENV_F32>;
+  v.fwd[ENV_F64] = nullptr;
+  v.fwd[ENV_BF16] = fwd_launch<Eng, ENV_BF16>;
+  v.fwd[ENV_F16] = fwd_launch<Eng, ENV_F16>;
+  v.inv[ENV_F32] = inv_launch<Eng, ENV_F32>;
+  v.inv[ENV_F64] = nullptr;
+  v.inv[ENV_BF16] = inv_launch<Eng, ENV_BF16>;
+  v.inv[ENV_F16] = inv_launch<Eng, ENV_F16>;
+  return v;
+}
+
+// StaticEngine<M, log2 rows per block, min blocks per SM, radices...>; the
+// first variant listed for a length is the default before tuning.
+#define QTAM_V(M, NBS, MINB, ...) \
+  make_variant<StaticEngine<M, NBS, MINB, __VA_ARGS__>>(#M ":" #__VA_ARGS__ " rows/blk 2^" #NBS " minblk " #MINB)
+const RowVariant kVariants[] = {
+    QTAM_V(4800, 0, 3, 16, 20, 15),
+    QTAM_V(4800, 0, 4, 16, 20, 15),
+    QTAM_V(4800, 0, 3, 16, 15, 20),
+    QTAM_V(4800, 0, 3, 16, 12, 25),
+    QTAM_V(4800, 0, 2, 16, 20, 15),
+    QTAM_V(4800, 0, 4, 8, 6, 10, 10),
+    QTAM_V(2400, 0, 3, 16, 10, 15),
+    QTAM_V(2400, 1, 2, 16, 10, 15),
+    QTAM_V(2400, 0, 4, 16, 10, 15),
+    QTAM_V(1200, 1, 2, 16, 15, 5),
+    QTAM_V(1200, 2, 2, 16, 3, 25),
+    QTAM_V(600, 3, 2, 8, 3, 25),
+    QTAM_V(600, 2, 2, 8, 15, 5),
+    QTAM_V(600, 2, 3, 8, 15, 5),
+    QTAM_V(500, 3, 2, 4, 5, 25),
+    QTAM_V(300, 3, 2, 12, 25),
+    QTAM_V(300, 4, 2, 4, 3, 25),
+    QTAM_V(150, 4, 2, 6, 25),
+    QTAM_V(75, 5, 2, 3, 25),
+    QTAM_V(75, 4, 3, 3, 25),
+};
+#undef QTAM_V
+
 }  // namespace
+
+int row_variant_count() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
+const RowVariant* row_variant(int i) { return (i >= 0 && i < row_variant_count()) ? &kVariants[i] : nullptr; }
 
 template <typename T>
 cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_rows, int64_t Nr, const cplx<T>* X,
                                 void* y, int env, int64_t B, const cplx<T>* twM, cudaStream_t st) {
-  const int64_t blocks = B * n_rows;
-  if (blocks == 0) return cudaSuccess;
+  const int64_t units = B * n_rows;
+  if (units == 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    if (const RowVariant* v = row_variant(c.variant)) return v->fwd[env](rows, n_rows, Nr, X, y, B, twM, st);
+  }
+  GenericEngine eng{c.rp};
+  const unsigned blocks = (unsigned)units;
   if constexpr (sizeof(T) == 4) {
     switch (env) {
       case ENV_BF16:
         allow_smem((const void*)k_rows_forward<T, ENV_BF16>, c.smem);
-        k_rows_forward<T, ENV_BF16><<<(unsigned)blocks, c.threads, c.smem, st>>>(
-            c.rp, rows, n_rows, Nr, X, static_cast<__nv_bfloat162*>(y), twM);
+        k_rows_forward<T, ENV_BF16><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
+                                                                       static_cast<__nv_bfloat162*>(y), units, twM);
         break;
       case ENV_F16:
         allow_smem((const void*)k_rows_forward<T, ENV_F16>, c.smem);
-        k_rows_forward<T, ENV_F16><<<(unsigned)blocks, c.threads, c.smem, st>>>(
-            c.rp, rows, n_rows, Nr, X, static_cast<__half2*>(y), twM);
+        k_rows_forward<T, ENV_F16><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
+                                                                      static_cast<__half2*>(y), units, twM);
         break;
       default:
         allow_smem((const void*)k_rows_forward<T, ENV_F32>, c.smem);
-        k_rows_forward<T, ENV_F32><<<(unsigned)blocks, c.threads, c.smem, st>>>(
-            c.rp, rows, n_rows, Nr, X, static_cast<float2*>(y), twM);
+        k_rows_forward<T, ENV_F32><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
+                                                                      static_cast<float2*>(y), units, twM);
     }
   } else {
     allow_smem((const void*)k_rows_forward<T, ENV_F64>, c.smem);
-    k_rows_forward<T, ENV_F64><<<(unsigned)blocks, c.threads, c.smem, st>>>(c.rp, rows, n_rows, Nr, X,
-                                                                          static_cast<double2*>(y), twM);
+    k_rows_forward<T, ENV_F64><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
+                                                                  static_cast<double2*>(y), units, twM);
   }
   return cudaGetLastError();
 }
@@ -166,29 +339,35 @@ template <typename T>
 cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const int* row_list, int n_sel, int n_rows,
                                 int64_t Nr, const void* y, int env, cplx<T>* A, int64_t B, const cplx<T>* twM,
                                 cudaStream_t st) {
-  const int64_t blocks = B * n_sel;
-  if (blocks == 0) return cudaSuccess;
+  const int64_t units = B * n_sel;
+  if (units == 0) return cudaSuccess;
+  if constexpr (sizeof(T) == 4) {
+    if (const RowVariant* v = row_variant(c.variant))
+      return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, twM, st);
+  }
+  GenericEngine eng{c.rp};
+  const unsigned blocks = (unsigned)units;
   if constexpr (sizeof(T) == 4) {
     switch (env) {
       case ENV_BF16:
         allow_smem((const void*)k_rows_inverse<T, ENV_BF16>, c.smem);
-        k_rows_inverse<T, ENV_BF16><<<(unsigned)blocks, c.threads, c.smem, st>>>(
-            c.rp, rows, row_list, n_sel, n_rows, Nr, static_cast<const __nv_bfloat162*>(y), A, twM);
+        k_rows_inverse<T, ENV_BF16><<<blocks, c.threads, c.smem, st>>>(
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __nv_bfloat162*>(y), A, units, twM);
         break;
       case ENV_F16:
         allow_smem((const void*)k_rows_inverse<T, ENV_F16>, c.smem);
-        k_rows_inverse<T, ENV_F16><<<(unsigned)blocks, c.threads, c.smem, st>>>(
-            c.rp, rows, row_list, n_sel, n_rows, Nr, static_cast<const __half2*>(y), A, twM);
+        k_rows_inverse<T, ENV_F16><<<blocks, c.threads, c.smem, st>>>(
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __half2*>(y), A, units, twM);
         break;
       default:
         allow_smem((const void*)k_rows_inverse<T, ENV_F32>, c.smem);
-        k_rows_inverse<T, ENV_F32><<<(unsigned)blocks, c.threads, c.smem, st>>>(
-            c.rp, rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, twM);
+        k_rows_inverse<T, ENV_F32><<<blocks, c.threads, c.smem, st>>>(
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, twM);
     }
   } else {
     allow_smem((const void*)k_rows_inverse<T, ENV_F64>, c.smem);
-    k_rows_inverse<T, ENV_F64><<<(unsigned)blocks, c.threads, c.smem, st>>>(
-        c.rp, rows, row_list, n_sel, n_rows, Nr, static_cast<const double2*>(y), A, twM);
+    k_rows_inverse<T, ENV_F64><<<blocks, c.threads, c.smem, st>>>(
+        eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const double2*>(y), A, units, twM);
   }
   return cudaGetLastError();
 }

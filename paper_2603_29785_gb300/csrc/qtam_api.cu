@@ -18,6 +18,7 @@
 // the library, done here once per plan (and once per new plane mask).
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <map>
 #include <mutex>
@@ -545,6 +546,14 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   }
   pl->rc.threads = threads_for(pl->rc.rp, 0);
   pl->rc.smem = smem_for(pl->rc.rp, 0, pl->cplx_size());
+  pl->rc.variant = -1;
+  if (!dbl) {
+    for (int v = 0; v < row_variant_count(); ++v)
+      if (row_variant(v)->M == pl->M) {
+        pl->rc.variant = v;   // first registered variant for this length
+        break;
+      }
+  }
   if (pl->rc.threads > kMaxThreads || pl->rc.smem > (size_t)kMaxSmem) {
     free_plan(pl);
     return fail(QTAM_ERR_UNSUPPORTED_SIZE, "n_out too large for one thread block");
@@ -611,6 +620,48 @@ qtam_status qtam_plan_info(qtam_plan_t pl, qtam_plan_info_t* o) {
     o->kept_bins = it->second.kept;
   }
   o->device_bytes = (int64_t)pl->device_bytes;
+  o->row_variant = pl->rc.variant;
+  return QTAM_OK;
+}
+
+qtam_status qtam_plan_variants(qtam_plan_t pl, int32_t* ids, int32_t capacity, int32_t* count) {
+  if (!pl || !count || capacity < 0 || (capacity > 0 && !ids)) return fail(QTAM_ERR_INVALID_ARG, "bad argument");
+  int32_t n = 0;
+  auto push = [&](int32_t id) {
+    if (n < capacity) ids[n] = id;
+    ++n;
+  };
+  push(-1);
+  if (pl->compute == QTAM_DTYPE_F32)
+    for (int v = 0; v < row_variant_count(); ++v)
+      if (row_variant(v)->M == pl->M) push(v);
+  *count = n;
+  return QTAM_OK;
+}
+
+qtam_status qtam_plan_set_variant(qtam_plan_t pl, int32_t id) {
+  if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
+  if (id != -1) {
+    const RowVariant* v = row_variant(id);
+    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32)
+      return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length or dtype");
+  }
+  pl->rc.variant = id;
+  return QTAM_OK;
+}
+
+qtam_status qtam_variant_describe(int32_t id, char* name, size_t capacity, int32_t* threads, int32_t* rows_per_block) {
+  if (id == -1) {
+    if (name && capacity) std::snprintf(name, capacity, "runtime mixed-radix engine");
+    if (threads) *threads = 0;
+    if (rows_per_block) *rows_per_block = 1;
+    return QTAM_OK;
+  }
+  const RowVariant* v = row_variant(id);
+  if (!v) return fail(QTAM_ERR_INVALID_ARG, "unknown variant");
+  if (name && capacity) std::snprintf(name, capacity, "%s", v->name);
+  if (threads) *threads = v->threads;
+  if (rows_per_block) *rows_per_block = v->rows_per_block;
   return QTAM_OK;
 }
 

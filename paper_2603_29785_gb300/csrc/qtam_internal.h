@@ -41,12 +41,31 @@ struct LongCfg {
 };
 
 struct RowCfg {
-  RadixPlan rp;  // radices of M
+  RadixPlan rp;  // radices of M (runtime engine)
   int threads;
   size_t smem;
+  int variant;   // index of a compile-time row-kernel variant, -1 = runtime engine
 };
 
 enum EnvKind { ENV_F32 = 0, ENV_F64 = 1, ENV_BF16 = 2, ENV_F16 = 3 };
+
+// A compile-time row-kernel variant (FP32 compute): fixed M, radix sequence,
+// rows per block and occupancy target.  fwd/inv are indexed by EnvKind.
+using RowFwdFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const float2*, void*, int64_t, const float2*,
+                                 cudaStream_t);
+using RowInvFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
+                                 const float2*, cudaStream_t);
+struct RowVariant {
+  int M;
+  int rows_per_block;
+  int threads;
+  size_t smem;
+  const char* name;
+  RowFwdFn fwd[4];
+  RowInvFn inv[4];
+};
+int row_variant_count();
+const RowVariant* row_variant(int i);   // nullptr when out of range
 
 // ---- launchers (kernels_long.cu) ----
 // z: [B][n] complex view of the real input; U: [B][n]; Z: [B][n]; X: [B][n+1]

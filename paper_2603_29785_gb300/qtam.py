@@ -54,7 +54,7 @@ class qtam_plan_info_t(ctypes.Structure):
         ("max_window", ctypes.c_int32), ("compute_dtype", ctypes.c_int32), ("envelope_dtype", ctypes.c_int32),
         ("fft_n1", ctypes.c_int32), ("fft_n2", ctypes.c_int32), ("envelope_bytes_per_segment", ctypes.c_int64),
         ("band_bins", ctypes.c_int64), ("p_floor_rel", ctypes.c_double), ("kappa", ctypes.c_double),
-        ("kept_bins", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+        ("kept_bins", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("row_variant", ctypes.c_int32),
     ]
 
 
@@ -71,6 +71,10 @@ SIGNATURES = {
     "qtam_plan_rows": (ctypes.c_int, [_P, _P, _P, _P, _P]),
     "qtam_frame_operator": (ctypes.c_int, [_P, _U64, _P]),
     "qtam_workspace_size": (ctypes.c_int, [_P, _I64, ctypes.POINTER(_SZ)]),
+    "qtam_plan_variants": (ctypes.c_int, [_P, _P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]),
+    "qtam_plan_set_variant": (ctypes.c_int, [_P, ctypes.c_int32]),
+    "qtam_variant_describe": (ctypes.c_int, [ctypes.c_int32, ctypes.c_char_p, _SZ, ctypes.POINTER(ctypes.c_int32),
+                                             ctypes.POINTER(ctypes.c_int32)]),
     "qtam_forward": (ctypes.c_int, [_P, _P, _I64, _P, _P, _SZ, _P]),
     "qtam_inverse": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P, _SZ, _P]),
     "qtam_stage_spectrum": (ctypes.c_int, [_P, _P, _I64, _P, _P, _SZ, _P]),
@@ -186,6 +190,25 @@ def qtam_workspace_size(plan, batch: int) -> int:
     s = _SZ()
     _check(lib().qtam_workspace_size(plan, int(batch), ctypes.byref(s)))
     return s.value
+
+
+def qtam_plan_variants(plan) -> list[int]:
+    n = ctypes.c_int32()
+    _check(lib().qtam_plan_variants(plan, None, 0, ctypes.byref(n)))
+    ids = np.zeros(max(1, n.value), np.int32)
+    _check(lib().qtam_plan_variants(plan, ids.ctypes.data, n.value, ctypes.byref(n)))
+    return [int(v) for v in ids[: n.value]]
+
+
+def qtam_plan_set_variant(plan, variant: int):
+    _check(lib().qtam_plan_set_variant(plan, int(variant)))
+
+
+def qtam_variant_describe(variant: int) -> dict:
+    buf = ctypes.create_string_buffer(128)
+    t, r = ctypes.c_int32(), ctypes.c_int32()
+    _check(lib().qtam_variant_describe(int(variant), buf, 128, ctypes.byref(t), ctypes.byref(r)))
+    return {"id": int(variant), "name": buf.value.decode(), "threads": t.value, "rows_per_block": r.value}
 
 
 def qtam_forward(plan, x, batch, y, workspace, workspace_bytes, stream=None):
