@@ -34,13 +34,15 @@ struct GenLong {
   }
 };
 template <int M_, int NBS_, int... Rs> struct StatLong {
+  static constexpr int nrad = sizeof...(Rs);
+  static constexpr int radices[nrad] = {Rs...};
   static constexpr int NT = StaticThreads<M_, NBS_, Rs...>::value;
   static constexpr int MINB = NT >= 512 ? 1 : 512 / NT;   // at least 512 threads per SM
   __device__ __forceinline__ int m() const { return M_; }
   __device__ __forceinline__ int nb_shift() const { return NBS_; }
   template <int S, typename V, class L, class St>
-  __device__ __forceinline__ void run(V* sm, const V* tw, int twstride, const L& ld, const St& st) const {
-    StaticFFT<S, M_, NT, NBS_, Rs...>::run(sm, tw, twstride, ld, st);
+  __device__ __forceinline__ void run(V* sm, const V* tws, int, const L& ld, const St& st) const {
+    StaticFFT<S, M_, NT, NBS_, Rs...>::run(sm, tws, ld, st);
   }
   static size_t smem_bytes(size_t elem) { return StaticFFT<1, M_, NT, NBS_, Rs...>::smem_elems() * elem; }
 };
@@ -67,7 +69,8 @@ template <typename V> struct StoreRowsTransposed {
 
 template <class Eng, typename T>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_col_forward(Eng eng, int n, int n2, const cplx<T>* __restrict__ z,
-                                                          cplx<T>* __restrict__ U, const cplx<T>* __restrict__ twn) {
+                                                          cplx<T>* __restrict__ U, const cplx<T>* __restrict__ twn,
+                                                          const cplx<T>* __restrict__ ftw) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -75,12 +78,12 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_col_forward(Eng eng, int
   const int c0 = blockIdx.x << eng.nb_shift();
   LoadColumns<V> ld{z + seg * n, n2, c0};
   StoreColumnsTwiddled<V> stv{U + seg * n, twn, n2, c0};
-  eng.template run<-1>(sm, twn, n / eng.m(), ld, stv);
+  eng.template run<-1>(sm, ftw, n / eng.m(), ld, stv);
 }
 
 template <class Eng, typename T>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_row_forward(Eng eng, int n, int n1, const cplx<T>* __restrict__ U,
-                                                          cplx<T>* __restrict__ Z, const cplx<T>* __restrict__ twn) {
+                                                          cplx<T>* __restrict__ Z, const cplx<T>* __restrict__ ftw) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -88,7 +91,7 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_row_forward(Eng eng, int
   const int r0 = blockIdx.x << eng.nb_shift();
   LoadRows<V> ld{U + seg * n, eng.m(), r0};
   StoreRowsTransposed<V> stv{Z + seg * n, n1, r0};
-  eng.template run<-1>(sm, twn, n / eng.m(), ld, stv);
+  eng.template run<-1>(sm, ftw, n / eng.m(), ld, stv);
 }
 
 // w_N^k for k in [0, n]: table holds k <= n/2; w_N^(n-k) = -conj(w_N^k)
@@ -160,7 +163,8 @@ template <class Eng, typename T>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_row_inverse(Eng eng, int n, int n1, const cplx<T>* __restrict__ A,
                                                           const T* __restrict__ invP, cplx<T>* __restrict__ Vb,
                                                           const cplx<T>* __restrict__ twn,
-                                                          const cplx<T>* __restrict__ twN, T scale) {
+                                                          const cplx<T>* __restrict__ twN, T scale,
+                                                          const cplx<T>* __restrict__ ftw) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -168,12 +172,12 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_row_inverse(Eng eng, int
   const int r0 = blockIdx.x << eng.nb_shift();
   LoadUntangleInverse<T> ld{A + seg * (int64_t)(n + 1), invP, twN, n, n1, r0, scale};
   StoreRowsTwiddledConj<V> stv{Vb + seg * n, twn, eng.m(), r0};
-  eng.template run<+1>(sm, twn, n / eng.m(), ld, stv);
+  eng.template run<+1>(sm, ftw, n / eng.m(), ld, stv);
 }
 
 template <class Eng, typename T>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_col_inverse(Eng eng, int n, int n2, const cplx<T>* __restrict__ Vb,
-                                                          cplx<T>* __restrict__ xout, const cplx<T>* __restrict__ twn) {
+                                                          cplx<T>* __restrict__ xout, const cplx<T>* __restrict__ ftw) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -181,7 +185,7 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_col_inverse(Eng eng, int
   const int c0 = blockIdx.x << eng.nb_shift();
   LoadColumns<V> ld{Vb + seg * n, n2, c0};
   StoreColumns<V> stv{xout + seg * n, n2, c0};
-  eng.template run<+1>(sm, twn, n / eng.m(), ld, stv);
+  eng.template run<+1>(sm, ftw, n / eng.m(), ld, stv);
 }
 
 constexpr int64_t kMaxGridY = 65535;
@@ -204,27 +208,49 @@ void launch_pass(K kernel, const Eng& eng, size_t smem, dim3 g, cudaStream_t st,
 
 // Call f(engine, smem) with the static engine for (m, nbs) when one exists
 // (FP32), else with the runtime engine.
-#define QTAM_CASE(M, NBS, ...)                   \
-  case M: {                                      \
-    using E = StatLong<M, NBS, __VA_ARGS__>;     \
-    f(E(), E::smem_bytes(sizeof(float2)));       \
-    return;                                      \
+#define QTAM_CASE(M, NBS, ...)                                     \
+  case M: {                                                        \
+    using E = StatLong<M, NBS, __VA_ARGS__>;                       \
+    f(E(), E::smem_bytes(sizeof(float2)), (const cplx<T>*)stw);    \
+    return;                                                        \
   }
 
+// Call f(engine, smem bytes, engine twiddles): the static engine for
+// (m, nbs) when one exists (FP32) and its tables were built, else the
+// runtime engine with the plan's length-n table.
 template <typename T, class F>
-void with_engine(const RadixPlan& rp, int nbs, int static_nbs, size_t gen_smem, F&& f) {
+void with_engine(const RadixPlan& rp, int nbs, int static_nbs, size_t gen_smem, const void* stw,
+                 const cplx<T>* twn, F&& f) {
   if constexpr (sizeof(T) == 4) {
-    if (nbs == static_nbs && static_nbs == 4) {
+    if (stw && nbs == static_nbs && static_nbs == 4) {
       switch (rp.m) { QTAM_LONG_CASES(QTAM_CASE, 4) default: break; }
-    } else if (nbs == static_nbs && static_nbs == 2) {
+    } else if (stw && nbs == static_nbs && static_nbs == 2) {
       switch (rp.m) { QTAM_LONG_CASES(QTAM_CASE, 2) default: break; }
     }
   }
-  f(GenLong{rp, nbs}, gen_smem);
+  f(GenLong{rp, nbs}, gen_smem, twn);
 }
 #undef QTAM_CASE
 
+#define QTAM_RADICES(M, NBS, ...)                   \
+  case M: {                                         \
+    using E = StatLong<M, NBS, __VA_ARGS__>;        \
+    *nst = E::nrad;                                 \
+    for (int i = 0; i < E::nrad; ++i) r[i] = E::radices[i]; \
+    return true;                                    \
+  }
+
 }  // namespace
+
+bool long_static_radices(int m, int nbs, int* r, int* nst) {
+  if (nbs == 4) {
+    switch (m) { QTAM_LONG_CASES(QTAM_RADICES, 4) default: break; }
+  } else if (nbs == 2) {
+    switch (m) { QTAM_LONG_CASES(QTAM_RADICES, 2) default: break; }
+  }
+  return false;
+}
+#undef QTAM_RADICES
 
 template <typename T>
 cudaError_t launch_spectrum(const LongCfg& c, const cplx<T>* z, cplx<T>* U, cplx<T>* Z, cplx<T>* X, int64_t B,
@@ -232,15 +258,15 @@ cudaError_t launch_spectrum(const LongCfg& c, const cplx<T>* z, cplx<T>* U, cplx
   for (int64_t s0 = 0; s0 < B; s0 += kMaxGridY) {
     const int64_t nb = (B - s0) < kMaxGridY ? (B - s0) : kMaxGridY;
     const int64_t off = s0 * c.n;
-    with_engine<T>(c.rp1, c.col_nbs, 4, c.col_smem, [&](auto eng, size_t smem) {
+    with_engine<T>(c.rp1, c.col_nbs, 4, c.col_smem, c.stw_col, twn, [&](auto eng, size_t smem, const cplx<T>* ftw) {
       using E = decltype(eng);
       dim3 g(c.n2 >> c.col_nbs, (unsigned)nb);
-      launch_pass(k_col_forward<E, T>, eng, smem, g, st, c.n, c.n2, z + off, U + off, twn);
+      launch_pass(k_col_forward<E, T>, eng, smem, g, st, c.n, c.n2, z + off, U + off, twn, ftw);
     });
-    with_engine<T>(c.rp2, c.row_nbs, 2, c.row_smem, [&](auto eng, size_t smem) {
+    with_engine<T>(c.rp2, c.row_nbs, 2, c.row_smem, c.stw_row, twn, [&](auto eng, size_t smem, const cplx<T>* ftw) {
       using E = decltype(eng);
       dim3 g(c.n1 >> c.row_nbs, (unsigned)nb);
-      launch_pass(k_row_forward<E, T>, eng, smem, g, st, c.n, c.n1, (const cplx<T>*)(U + off), Z + off, twn);
+      launch_pass(k_row_forward<E, T>, eng, smem, g, st, c.n, c.n1, (const cplx<T>*)(U + off), Z + off, ftw);
     });
     dim3 g3((unsigned)((c.n / 2 + 1 + 255) / 256), (unsigned)nb);
     k_untangle_forward<T><<<g3, 256, 0, st>>>(c.n, Z + off, X + s0 * (int64_t)(c.n + 1), twN);
@@ -254,16 +280,16 @@ cudaError_t launch_synthesis(const LongCfg& c, const cplx<T>* A, const T* invP, 
   for (int64_t s0 = 0; s0 < B; s0 += kMaxGridY) {
     const int64_t nb = (B - s0) < kMaxGridY ? (B - s0) : kMaxGridY;
     const int64_t off = s0 * c.n;
-    with_engine<T>(c.rp2, c.row_nbs, 2, c.row_smem, [&](auto eng, size_t smem) {
+    with_engine<T>(c.rp2, c.row_nbs, 2, c.row_smem, c.stw_row, twn, [&](auto eng, size_t smem, const cplx<T>* ftw) {
       using E = decltype(eng);
       dim3 g(c.n1 >> c.row_nbs, (unsigned)nb);
       launch_pass(k_row_inverse<E, T>, eng, smem, g, st, c.n, c.n1, A + s0 * (int64_t)(c.n + 1), invP, Vb + off,
-                  twn, twN, (T)1 / (T)c.n);
+                  twn, twN, (T)1 / (T)c.n, ftw);
     });
-    with_engine<T>(c.rp1, c.col_nbs, 4, c.col_smem, [&](auto eng, size_t smem) {
+    with_engine<T>(c.rp1, c.col_nbs, 4, c.col_smem, c.stw_col, twn, [&](auto eng, size_t smem, const cplx<T>* ftw) {
       using E = decltype(eng);
       dim3 g(c.n2 >> c.col_nbs, (unsigned)nb);
-      launch_pass(k_col_inverse<E, T>, eng, smem, g, st, c.n, c.n2, (const cplx<T>*)(Vb + off), xout + off, twn);
+      launch_pass(k_col_inverse<E, T>, eng, smem, g, st, c.n, c.n2, (const cplx<T>*)(Vb + off), xout + off, ftw);
     });
   }
   return cudaGetLastError();

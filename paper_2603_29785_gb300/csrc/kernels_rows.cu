@@ -58,19 +58,30 @@ template <> struct Env<double2, ENV_F64> {
 // Per-thread view of the row it works on.  Every call a thread makes uses
 // the same interleave slot b = threadIdx.x mod 2^NBS (block sizes are whole
 // warps), so the row descriptor is read once, not per element.
+//
+// The row's usable offsets are d in [dlo, dhi] = [-h, h] cut to bins
+// 0..N/2; baseband position i holds d = i for i <= dhi and d = i - M for
+// i >= M + dlo.  When h^2 < 2^24, (h - |d|)(h + |d|) = h^2 - d^2 is formed
+// exactly in floating point (both squares and their difference are exact).
 template <typename T> struct RowCtx {
-  int kc, h, M, nhalf;
-  T c, inv_h2;
-  bool valid;
-  // band offset of baseband position i (i = d mod M); false outside the band
+  int kc, h, M, dhi, mlo;
+  T c, inv_h2, h2;
+  bool exact_f;
   __device__ __forceinline__ bool offset(int i, int& d, int& f) const {
-    d = i <= h ? i : i - M;
+    d = i <= dhi ? i : i - M;
     f = kc + d;
-    return valid && (i <= h || i >= M - h) && f >= 0 && f <= nhalf;
+    return i <= dhi || i >= mlo;
   }
   __device__ __forceinline__ T weight(int d) const {
-    const int a = d < 0 ? -d : d;
-    return c * bisquare<T>(a, h, inv_h2);
+    T u;
+    if (exact_f) {
+      const T df = (T)d;
+      u = (h2 - df * df) * inv_h2;
+    } else {
+      const int a = d < 0 ? -d : d;
+      u = (T)(h - a) * (T)(h + a) * inv_h2;
+    }
+    return c * (u * u);
   }
 };
 
@@ -130,13 +141,15 @@ struct GenericEngine {
 
 template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
   static constexpr int M = M_;
+  static constexpr int nrad = sizeof...(Rs);
+  static constexpr int radices[nrad] = {Rs...};
   static constexpr int NBS = NBS_;
   static constexpr int NT = StaticThreads<M_, NBS_, Rs...>::value;
   static constexpr int MINB = MINB_;
   __device__ __forceinline__ int m() const { return M; }
   template <int S, typename V, class L, class St>
-  __device__ __forceinline__ void run(V* sm, const V* tw, const L& ld, const St& st) const {
-    StaticFFT<S, M, NT, NBS, Rs...>::run(sm, tw, 1, ld, st);
+  __device__ __forceinline__ void run(V* sm, const V* tws, const L& ld, const St& st) const {
+    StaticFFT<S, M, NT, NBS, Rs...>::run(sm, tws, ld, st);
   }
   static size_t smem_bytes(size_t elem) { return StaticFFT<1, M, NT, NBS, Rs...>::smem_elems() * elem; }
 };
@@ -144,18 +157,24 @@ template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
 template <typename T>
 __device__ __forceinline__ RowCtx<T> row_ctx(const RowDev<T>* rows, int row, int M, int64_t Nr, bool valid, bool inv) {
   RowCtx<T> r;
+  r.M = M;
   if (valid) {
     const RowDev<T> rd = rows[row];
+    const int nhalf = (int)(Nr - 1);
     r.kc = rd.kc;
     r.h = rd.h;
     r.c = inv ? rd.c_inv : rd.c_fwd;
     r.inv_h2 = rd.inv_h2;
+    r.h2 = (T)rd.h * (T)rd.h;
+    r.exact_f = rd.h < 4096;
+    r.dhi = min(rd.h, nhalf - rd.kc);     // may be < 0: no non-negative offset
+    r.mlo = M + max(-rd.h, -rd.kc);       // may be > M - 1: no negative offset
+    if (r.dhi < -1) r.dhi = -1;
   } else {
-    r.kc = 0; r.h = 0; r.c = 0; r.inv_h2 = 0;
+    r.kc = 0; r.h = 1; r.c = 0; r.inv_h2 = 0; r.h2 = 1; r.exact_f = true;
+    r.dhi = -1;
+    r.mlo = M;                            // nothing in band
   }
-  r.M = M;
-  r.nhalf = (int)(Nr - 1);
-  r.valid = valid;
   return r;
 }
 
@@ -256,6 +275,8 @@ template <class Eng> RowVariant make_variant(const char* name) {
   v.threads = Eng::NT;
   v.smem = Eng::smem_bytes(sizeof(float2));
   v.name = name;
+  v.nst = Eng::nrad;
+  for (int i = 0; i < Eng::nrad; ++i) v.r[i] = Eng::radices[i];
   v.fwd[ENV_F32] = fwd_launch<Eng, ENV_F32>;
   v.fwd[ENV_F64] = nullptr;
   v.fwd[ENV_BF16] = fwd_launch<Eng, ENV_BF16>;
@@ -272,12 +293,12 @@ template <class Eng> RowVariant make_variant(const char* name) {
 #define QTAM_V(M, NBS, MINB, ...) \
   make_variant<StaticEngine<M, NBS, MINB, __VA_ARGS__>>(#M ":" #__VA_ARGS__ " rows/blk 2^" #NBS " minblk " #MINB)
 const RowVariant kVariants[] = {
-    QTAM_V(4800, 0, 3, 16, 20, 15),
     QTAM_V(4800, 0, 4, 16, 20, 15),
+    QTAM_V(4800, 0, 3, 16, 20, 15),
     QTAM_V(4800, 0, 3, 16, 15, 20),
-    QTAM_V(4800, 0, 3, 16, 12, 25),
     QTAM_V(4800, 0, 2, 16, 20, 15),
-    QTAM_V(4800, 0, 4, 8, 6, 10, 10),
+    QTAM_V(4800, 0, 3, 8, 6, 10, 10),
+    QTAM_V(4800, 0, 2, 16, 12, 25),
     QTAM_V(2400, 0, 3, 16, 10, 15),
     QTAM_V(2400, 1, 2, 16, 10, 15),
     QTAM_V(2400, 0, 4, 16, 10, 15),
@@ -285,13 +306,11 @@ const RowVariant kVariants[] = {
     QTAM_V(1200, 2, 2, 16, 3, 25),
     QTAM_V(600, 3, 2, 8, 3, 25),
     QTAM_V(600, 2, 2, 8, 15, 5),
-    QTAM_V(600, 2, 3, 8, 15, 5),
     QTAM_V(500, 3, 2, 4, 5, 25),
     QTAM_V(300, 3, 2, 12, 25),
     QTAM_V(300, 4, 2, 4, 3, 25),
     QTAM_V(150, 4, 2, 6, 25),
     QTAM_V(75, 5, 2, 3, 25),
-    QTAM_V(75, 4, 3, 3, 25),
 };
 #undef QTAM_V
 
@@ -306,7 +325,8 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
   const int64_t units = B * n_rows;
   if (units == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (const RowVariant* v = row_variant(c.variant)) return v->fwd[env](rows, n_rows, Nr, X, y, B, twM, st);
+    if (const RowVariant* v = row_variant(c.variant))
+      return v->fwd[env](rows, n_rows, Nr, X, y, B, static_cast<const float2*>(c.stw), st);
   }
   GenericEngine eng{c.rp};
   const unsigned blocks = (unsigned)units;
@@ -343,7 +363,7 @@ cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const in
   if (units == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
     if (const RowVariant* v = row_variant(c.variant))
-      return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, twM, st);
+      return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, static_cast<const float2*>(c.stw), st);
   }
   GenericEngine eng{c.rp};
   const unsigned blocks = (unsigned)units;

@@ -150,6 +150,9 @@ struct qtam_plan_s {
   void* d_twn = nullptr;
   void* d_twN = nullptr;
   size_t device_bytes = 0;
+  std::map<int, void*> variant_tw;   // stage twiddle tables per row-kernel variant
+  void* d_stw_col = nullptr;
+  void* d_stw_row = nullptr;
   std::mutex mu;
   std::map<uint64_t, MaskEntry> masks;
 
@@ -293,6 +296,18 @@ bool choose_long(int64_t n, bool dbl, LongCfg& lc) {
   return found;
 }
 
+// Build the stage twiddle tables of a compile-time radix sequence in FP64,
+// round to float once and upload them.
+qtam_status upload_stage_table(const int* r, int nst, void** dst, size_t& total) {
+  size_t n = 0;
+  stage_twiddles(r, nst, nullptr, &n);
+  if (n == 0) n = 1;
+  std::vector<double> d(2 * n, 0.0);
+  stage_twiddles(r, nst, d.data(), &n);
+  std::vector<float> f(d.begin(), d.end());
+  return upload(dst, f.data(), f.size() * sizeof(float), total);
+}
+
 template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
   std::vector<T> tw;
   size_t tot = 0;
@@ -313,6 +328,27 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
     rows[r].inv_h2 = (T)(1.0 / ((double)pl->h[r] * (double)pl->h[r]));
   }
   if ((s = upload(&pl->d_rows, rows.data(), rows.size() * sizeof(RowDev<T>), tot)) != QTAM_OK) return s;
+  if (sizeof(T) == 4) {
+    for (int v = 0; v < row_variant_count(); ++v) {
+      const RowVariant* rv = row_variant(v);
+      if (rv->M != pl->M) continue;
+      void* p = nullptr;
+      if ((s = upload_stage_table(rv->r, rv->nst, &p, tot)) != QTAM_OK) return s;
+      pl->variant_tw[v] = p;
+    }
+    int r[kMaxStages], nst = 0;
+    if (long_static_radices(pl->lc.n1, pl->lc.col_nbs, r, &nst)) {
+      if ((s = upload_stage_table(r, nst, &pl->d_stw_col, tot)) != QTAM_OK) return s;
+      pl->lc.stw_col = pl->d_stw_col;
+    }
+    if (long_static_radices(pl->lc.n2, pl->lc.row_nbs, r, &nst)) {
+      if ((s = upload_stage_table(r, nst, &pl->d_stw_row, tot)) != QTAM_OK) return s;
+      pl->lc.stw_row = pl->d_stw_row;
+    }
+    auto it = pl->variant_tw.find(pl->rc.variant);
+    pl->rc.stw = it == pl->variant_tw.end() ? nullptr : it->second;
+    if (pl->rc.variant >= 0 && !pl->rc.stw) pl->rc.variant = -1;
+  }
   pl->device_bytes += tot;
   return QTAM_OK;
 }
@@ -325,6 +361,9 @@ void free_plan(qtam_plan_s* pl) {
     cudaFree(pl->d_twM);
     cudaFree(pl->d_twn);
     cudaFree(pl->d_twN);
+    cudaFree(pl->d_stw_col);
+    cudaFree(pl->d_stw_row);
+    for (auto& kv : pl->variant_tw) cudaFree(kv.second);
     for (auto& kv : pl->masks) {
       cudaFree(kv.second.invP);
       cudaFree(kv.second.rows);
@@ -645,6 +684,11 @@ qtam_status qtam_plan_set_variant(qtam_plan_t pl, int32_t id) {
     const RowVariant* v = row_variant(id);
     if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32)
       return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length or dtype");
+  }
+  if (id >= 0 && pl->device >= 0) {
+    auto it = pl->variant_tw.find(id);
+    if (it == pl->variant_tw.end()) return fail(QTAM_ERR_INVALID_ARG, "variant tables were not built for this plan");
+    pl->rc.stw = it->second;
   }
   pl->rc.variant = id;
   return QTAM_OK;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
 #include <string>
 
 #include "fft_core.cuh"
@@ -31,6 +32,8 @@ template <typename T> struct RowDev {
 
 // Long real FFT of N = 2n samples as an n = n1 * n2 four-step complex FFT.
 struct LongCfg {
+  const void* stw_col = nullptr;   // stage twiddle tables of the static column engine (or null)
+  const void* stw_row = nullptr;   // ... of the static row engine
   int n;        // N / 2
   int n1, n2;   // column length n1 (stride n2), row length n2
   int col_nbs;  // log2 of columns per column-pass block
@@ -45,6 +48,7 @@ struct RowCfg {
   int threads;
   size_t smem;
   int variant;   // index of a compile-time row-kernel variant, -1 = runtime engine
+  const void* stw = nullptr;   // stage twiddle tables of that variant
 };
 
 enum EnvKind { ENV_F32 = 0, ENV_F64 = 1, ENV_BF16 = 2, ENV_F16 = 3 };
@@ -61,6 +65,8 @@ struct RowVariant {
   int threads;
   size_t smem;
   const char* name;
+  int nst;       // radix sequence of the compile-time FFT
+  int r[kMaxStages];
   RowFwdFn fwd[4];
   RowInvFn inv[4];
 };
@@ -87,6 +93,33 @@ template <typename T>
 cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const int* row_list, int n_sel, int n_rows,
                                 int64_t Nr, const void* y, int env, cplx<T>* A, int64_t B, const cplx<T>* twM,
                                 cudaStream_t st);
+
+// radix sequence of the static long-FFT engine used for a pass of length m
+// with 2^nbs interleaved transforms (FP32); false when the runtime engine runs
+bool long_static_radices(int m, int nbs, int* r, int* nst);
+
+// Stage twiddle tables of a compile-time radix sequence r[0..nst), stage 0
+// has none: for s >= 1 with NS = r_0 ... r_{s-1}, entries [i][k] (k fastest)
+// = exp(-2 pi i ik / (NS r_s)), i < r_s, k < NS.  Interleaved (re, im), FP64.
+inline void stage_twiddles(const int* r, int nst, double* out_or_null, size_t* count) {
+  size_t n = 0, ns = (size_t)r[0];
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int s = 1; s < nst; ++s) {
+    const size_t span = ns * (size_t)r[s];
+    for (int i = 0; i < r[s]; ++i)
+      for (size_t k = 0; k < ns; ++k) {
+        if (out_or_null) {
+          const size_t e = ((size_t)i * k) % span;
+          const double ang = two_pi * (double)e / (double)span;
+          out_or_null[2 * n] = std::cos(ang);
+          out_or_null[2 * n + 1] = -std::sin(ang);
+        }
+        ++n;
+      }
+    ns = span;
+  }
+  *count = n;
+}
 
 // ---- host helpers (qtam_api.cu) ----
 void set_last_error(const std::string& msg);   // message for qtam_last_error()
