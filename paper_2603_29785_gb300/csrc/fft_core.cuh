@@ -18,6 +18,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <utility>
+
 namespace qtam {
 
 // ---------------------------------------------------------------------------
@@ -132,61 +134,50 @@ template <int S> struct Dft<5, S> {
   }
 };
 
-// Twiddles of a composite radix: w_R^e = (cos 2 pi e/R, sin 2 pi e/R) for
-// e < R, built at compile time into constant memory and read at indices that
-// are compile-time constants after unrolling (constant-bank operands).
-template <int R, typename T> struct TwTab {
-  T c[R], s[R];
-};
-template <int R, typename T> constexpr TwTab<R, T> make_twtab() {
-  TwTab<R, T> t{};
-  for (int e = 0; e < R; ++e) {
-    t.c[e] = (T)ce_cos2pi(e, R);
-    t.s[e] = (T)ce_sin2pi(e, R);
-  }
-  return t;
-}
-template <int R> struct TwConst;
-#define QTAM_TWCONST(R)                                                            \
-  static __constant__ TwTab<R, float> kTwF##R = make_twtab<R, float>();            \
-  static __constant__ TwTab<R, double> kTwD##R = make_twtab<R, double>();          \
-  template <> struct TwConst<R> {                                                  \
-    __device__ __forceinline__ static float2 get(int e, float) {                   \
-      return make_float2(kTwF##R.c[e], kTwF##R.s[e]);                              \
-    }                                                                              \
-    __device__ __forceinline__ static double2 get(int e, double) {                 \
-      return make_double2(kTwD##R.c[e], kTwD##R.s[e]);                             \
-    }                                                                              \
-  };
-
 // composite R = R1 * R2: index j = R2 j1 + j2, output k = k1 + R1 k2
 //   b[j2][k1] = DFT_R1 over j1 of a[R2 j1 + j2];  b *= w_R^(S j2 k1);
 //   y[k1 + R1 k2] = DFT_R2 over j2 of b[j2][k1]
-// Plain unrolled loops: every array index is a compile-time constant, so the
-// arrays stay in registers.
+// The inner twiddles are compile-time constants (immediate operands); the
+// quarter turns among them reduce to swaps and negations.
+template <int E, int R, int S, typename V> __device__ __forceinline__ void twiddle_const(V& x) {
+  using T = decltype(V::x);
+  constexpr int e = E % R;
+  if constexpr (e == 0) {
+  } else if constexpr (4 * e == R) {           // w = S i
+    x = mul_si<S>(x);
+  } else if constexpr (2 * e == R) {           // w = -1
+    x = mk<V>(-x.x, -x.y);
+  } else if constexpr (4 * e == 3 * R) {       // w = -S i
+    x = mul_si<-S>(x);
+  } else {
+    constexpr T c = (T)ce_cos2pi(e, R);
+    constexpr T sn = (T)(S * ce_sin2pi(e, R));
+    x = mk<V>(x.x * c - x.y * sn, x.x * sn + x.y * c);
+  }
+}
+
 template <int R1, int R2, int S> struct DftComposite {
+  static constexpr int R = R1 * R2;
+  template <int J2, int... K1, typename V>
+  __device__ __forceinline__ static void twiddle_col(V* col, std::integer_sequence<int, K1...>) {
+    (twiddle_const<J2 * K1, R, S>(col[K1]), ...);
+  }
+  template <int... J2, typename V>
+  __device__ __forceinline__ static void columns(V* a, V* b, std::integer_sequence<int, J2...>) {
+    (column<J2>(a, b), ...);
+  }
+  template <int J2, typename V> __device__ __forceinline__ static void column(V* a, V* b) {
+    V col[R1];
+#pragma unroll
+    for (int j1 = 0; j1 < R1; ++j1) col[j1] = a[R2 * j1 + J2];
+    Dft<R1, S>::run(col);
+    twiddle_col<J2>(col, std::make_integer_sequence<int, R1>{});
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) b[J2 * R1 + k1] = col[k1];
+  }
   template <typename V> __device__ __forceinline__ static void run(V* a) {
-    using T = decltype(V::x);
-    constexpr int R = R1 * R2;
     V b[R];
-#pragma unroll
-    for (int j2 = 0; j2 < R2; ++j2) {
-      V col[R1];
-#pragma unroll
-      for (int j1 = 0; j1 < R1; ++j1) col[j1] = a[R2 * j1 + j2];
-      Dft<R1, S>::run(col);
-#pragma unroll
-      for (int k1 = 0; k1 < R1; ++k1) {
-        const int e = (j2 * k1) % R;
-        if (e == 0) {
-          b[j2 * R1 + k1] = col[k1];
-        } else {
-          V w = TwConst<R>::get(e, T());
-          if (S < 0) w.y = -w.y;
-          b[j2 * R1 + k1] = cmul(col[k1], w);
-        }
-      }
-    }
+    columns(a, b, std::make_integer_sequence<int, R2>{});
 #pragma unroll
     for (int k1 = 0; k1 < R1; ++k1) {
       V row[R2];
@@ -198,16 +189,6 @@ template <int R1, int R2, int S> struct DftComposite {
     }
   }
 };
-QTAM_TWCONST(6)
-QTAM_TWCONST(8)
-QTAM_TWCONST(9)
-QTAM_TWCONST(10)
-QTAM_TWCONST(12)
-QTAM_TWCONST(15)
-QTAM_TWCONST(16)
-QTAM_TWCONST(20)
-QTAM_TWCONST(25)
-QTAM_TWCONST(32)
 template <int S> struct Dft<6, S> : DftComposite<2, 3, S> {};
 template <int S> struct Dft<8, S> : DftComposite<2, 4, S> {};
 template <int S> struct Dft<9, S> : DftComposite<3, 3, S> {};

@@ -27,11 +27,6 @@ namespace qtam {
 
 namespace {
 
-template <typename T> __device__ __forceinline__ T bisquare(int a, int h, T inv_h2) {
-  const T u = (T)(h - a) * (T)(h + a) * inv_h2;   // 1 - (d/h)^2 without cancellation
-  return u * u;
-}
-
 // envelope storage conversions
 template <typename V, int E> struct Env;
 template <> struct Env<float2, ENV_F32> {
@@ -61,38 +56,42 @@ template <> struct Env<double2, ENV_F64> {
 //
 // The row's usable offsets are d in [dlo, dhi] = [-h, h] cut to bins
 // 0..N/2; baseband position i holds d = i for i <= dhi and d = i - M for
-// i >= M + dlo.  When h^2 < 2^24, (h - |d|)(h + |d|) = h^2 - d^2 is formed
-// exactly in floating point (both squares and their difference are exact).
-template <typename T> struct RowCtx {
+// i >= M + dlo.  The weight is c W'(d) = (kw (h^2 - d^2))^2 with
+// kw = sqrt(c)/h^2; with FEXACT (h < 4096) h^2 - d^2 is formed exactly in
+// floating point, otherwise as the integer product (h - |d|)(h + |d|).
+template <typename T, bool FEXACT> struct RowCtx {
   int kc, h, M, dhi, mlo;
-  T c, inv_h2, h2;
-  bool exact_f;
-  __device__ __forceinline__ bool offset(int i, int& d, int& f) const {
-    d = i <= dhi ? i : i - M;
-    f = kc + d;
-    return i <= dhi || i >= mlo;
+  T kw, h2;
+  __device__ __forceinline__ void locate(int i, bool& in, int& d) const {
+    const bool lo = i <= dhi;
+    in = lo || i >= mlo;
+    d = lo ? i : i - M;
   }
   __device__ __forceinline__ T weight(int d) const {
     T u;
-    if (exact_f) {
+    if constexpr (FEXACT) {
       const T df = (T)d;
-      u = (h2 - df * df) * inv_h2;
+      u = (h2 - df * df) * kw;
     } else {
       const int a = d < 0 ? -d : d;
-      u = (T)(h - a) * (T)(h + a) * inv_h2;
+      u = (T)(h - a) * (T)(h + a) * kw;
     }
-    return c * (u * u);
+    return u * u;
   }
 };
 
-template <typename T> struct LoadBand {
+template <typename T, bool FEXACT> struct LoadBand {
   using V = cplx<T>;
   const V* Xs;
-  RowCtx<T> r;
+  RowCtx<T, FEXACT> r;
   __device__ __forceinline__ V get(int, int i) const {
-    int d, f;
-    if (!r.offset(i, d, f)) return mk<V>((T)0, (T)0);
-    return cscale(Xs[f], r.weight(d));
+    bool in;
+    int d;
+    r.locate(i, in, d);
+    const T w = r.weight(d);
+    V x = mk<V>((T)0, (T)0);
+    if (in) x = Xs[r.kc + d];
+    return cscale(x, w);
   }
 };
 template <typename V, int E> struct StoreEnvelope {
@@ -117,14 +116,16 @@ template <> __device__ __forceinline__ void add_to<double2>(double2* p, double2 
   atomicAdd(&p->y, v.y);
 }
 
-template <typename T> struct AccumulateBand {
+template <typename T, bool FEXACT> struct AccumulateBand {
   using V = cplx<T>;
   V* As;
-  RowCtx<T> r;
+  RowCtx<T, FEXACT> r;
   __device__ __forceinline__ void put(int, int i, V v) const {
-    int d, f;
-    if (!r.offset(i, d, f)) return;
-    add_to(&As[f], cscale(v, r.weight(d)));
+    bool in;
+    int d;
+    r.locate(i, in, d);
+    const T w = r.weight(d);
+    if (in) add_to(&As[r.kc + d], cscale(v, w));
   }
 };
 
@@ -132,6 +133,7 @@ template <typename T> struct AccumulateBand {
 struct GenericEngine {
   RadixPlan rp;
   static constexpr int NBS = 0;
+  static constexpr bool FEXACT = false;
   __device__ __forceinline__ int m() const { return rp.m; }
   template <int S, typename V, class L, class St>
   __device__ __forceinline__ void run(V* sm, const V* tw, const L& ld, const St& st) const {
@@ -146,6 +148,8 @@ template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
   static constexpr int NBS = NBS_;
   static constexpr int NT = StaticThreads<M_, NBS_, Rs...>::value;
   static constexpr int MINB = MINB_;
+  static_assert(M_ <= 8192, "static variants need h < 4096 for the exact float window");
+  static constexpr bool FEXACT = true;
   __device__ __forceinline__ int m() const { return M; }
   template <int S, typename V, class L, class St>
   __device__ __forceinline__ void run(V* sm, const V* tws, const L& ld, const St& st) const {
@@ -154,24 +158,23 @@ template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
   static size_t smem_bytes(size_t elem) { return StaticFFT<1, M, NT, NBS, Rs...>::smem_elems() * elem; }
 };
 
-template <typename T>
-__device__ __forceinline__ RowCtx<T> row_ctx(const RowDev<T>* rows, int row, int M, int64_t Nr, bool valid, bool inv) {
-  RowCtx<T> r;
+template <typename T, bool FEXACT>
+__device__ __forceinline__ RowCtx<T, FEXACT> row_ctx(const RowDev<T>* rows, int row, int M, int64_t Nr, bool valid,
+                                                     bool inv) {
+  RowCtx<T, FEXACT> r;
   r.M = M;
   if (valid) {
     const RowDev<T> rd = rows[row];
     const int nhalf = (int)(Nr - 1);
     r.kc = rd.kc;
     r.h = rd.h;
-    r.c = inv ? rd.c_inv : rd.c_fwd;
-    r.inv_h2 = rd.inv_h2;
+    r.kw = inv ? rd.kw_inv : rd.kw_fwd;
     r.h2 = (T)rd.h * (T)rd.h;
-    r.exact_f = rd.h < 4096;
     r.dhi = min(rd.h, nhalf - rd.kc);     // may be < 0: no non-negative offset
     r.mlo = M + max(-rd.h, -rd.kc);       // may be > M - 1: no negative offset
     if (r.dhi < -1) r.dhi = -1;
   } else {
-    r.kc = 0; r.h = 1; r.c = 0; r.inv_h2 = 0; r.h2 = 1; r.exact_f = true;
+    r.kc = 0; r.h = 1; r.kw = 0; r.h2 = 1;
     r.dhi = -1;
     r.mlo = M;                            // nothing in band
   }
@@ -191,7 +194,7 @@ __device__ __forceinline__ void rows_forward_body(const Eng& eng, const RowDev<T
   const bool valid = unit < n_units;
   const int64_t seg = valid ? unit / n_rows : 0;
   const int row = valid ? (int)(unit - seg * n_rows) : 0;
-  LoadBand<T> ld{X + seg * Nr, row_ctx<T>(rows, row, M, Nr, valid, false)};
+  LoadBand<T, Eng::FEXACT> ld{X + seg * Nr, row_ctx<T, Eng::FEXACT>(rows, row, M, Nr, valid, false)};
   StoreEnvelope<V, E> stv{y + (valid ? unit : 0) * M, valid};
   eng.template run<+1>(sm, twM, ld, stv);
 }
@@ -211,7 +214,7 @@ __device__ __forceinline__ void rows_inverse_body(const Eng& eng, const RowDev<T
   const int64_t seg = valid ? unit / n_sel : 0;
   const int row = valid ? row_list[unit - seg * n_sel] : 0;
   LoadEnvelope<V, E> ld{y + (seg * n_rows + row) * M, valid};
-  AccumulateBand<T> stv{A + seg * Nr, row_ctx<T>(rows, row, M, Nr, valid, true)};
+  AccumulateBand<T, Eng::FEXACT> stv{A + seg * Nr, row_ctx<T, Eng::FEXACT>(rows, row, M, Nr, valid, true)};
   eng.template run<-1>(sm, twM, ld, stv);
 }
 

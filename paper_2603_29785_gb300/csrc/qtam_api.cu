@@ -326,6 +326,8 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
     rows[r].c_fwd = (T)(pl->c[r] / sMN);
     rows[r].c_inv = (T)(pl->c[r] * sNM);
     rows[r].inv_h2 = (T)(1.0 / ((double)pl->h[r] * (double)pl->h[r]));
+    rows[r].kw_fwd = (T)(std::sqrt(pl->c[r] / sMN) / ((double)pl->h[r] * (double)pl->h[r]));
+    rows[r].kw_inv = (T)(std::sqrt(pl->c[r] * sNM) / ((double)pl->h[r] * (double)pl->h[r]));
   }
   if ((s = upload(&pl->d_rows, rows.data(), rows.size() * sizeof(RowDev<T>), tot)) != QTAM_OK) return s;
   if (sizeof(T) == 4) {

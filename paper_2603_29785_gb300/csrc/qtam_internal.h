@@ -28,6 +28,8 @@ template <typename T> struct RowDev {
   T c_fwd;    // c_k / sqrt(M N): window normalisation times the forward renormalisation
   T c_inv;    // c_k sqrt(N / M): window normalisation times the synthesis re-scaling
   T inv_h2;   // 1 / h^2
+  T kw_fwd;   // sqrt(c_fwd) / h^2: window weight c_fwd W'(d) = (kw_fwd (h^2 - d^2))^2
+  T kw_inv;   // sqrt(c_inv) / h^2
 };
 
 // Long real FFT of N = 2n samples as an n = n1 * n2 four-step complex FFT.
