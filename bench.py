@@ -44,6 +44,10 @@ def parse():
     ap.add_argument("--cpu-sample-segments", type=int, default=4)
     ap.add_argument("--variant", type=int, default=None,
                     help="row-kernel variant id (default: chosen by the autotuner)")
+    ap.add_argument("--workload", default="64s", choices=["64s", "batched", "serving", "precision"],
+                    help="64s: the headline workload (default); batched: 512 uneven segments in one graph; "
+                         "serving: Poisson request stream; precision: envelope dtype sweep")
+    ap.add_argument("--duration", type=float, default=60.0, help="seconds of arrivals for --workload serving")
     return ap.parse_args()
 
 
@@ -321,12 +325,162 @@ def run_gpu(args, rank, world, local):
         dist.destroy_process_group()
 
 
+# ---------------------------------------------------------------------------- other workloads
+def _clock_wrap(fn, local):
+    clocks = ClockSampler(local)
+    clocks.start()
+    try:
+        out = fn()
+    finally:
+        clk = clocks.stop()
+    return out, clk
+
+
+def run_batched(args, local):
+    """512 uneven segments (1-32 s, 4096/16384 Hz), Q {8,16,32} x 128 rows:
+    forward + inverse of all segments captured as one CUDA graph, against the
+    plain path (one forward + one inverse call per segment, no graph)."""
+    import torch
+    from paper_2603_29785_gb300 import batch as qb, qtam
+    torch.cuda.set_device(local)
+    segs, rates = qb.uneven_workload(512, seed=0)
+    cache = qb.PlanCache((8.0, 16.0, 32.0), 20.0, 2048.0, 128, device=local)
+    ub = qb.UnevenBatch(segs, rates, cache, tune=True)
+    ub.capture()
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        ub.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed():
+        e0.record(st)
+        for _ in range(args.steps):
+            ub.replay()
+        e1.record(st)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+    ms, clk = _clock_wrap(timed, local)
+    # plain per-segment path: one forward and one inverse per segment, eager
+    per = []
+    for g in ub.groups:
+        for j in range(len(g.index)):
+            per.append((g.plan, g.x[j:j + 1], g.y[j:j + 1], g.xh[j:j + 1]))
+
+    def plain():
+        for p, x, y, xh in per:
+            p.forward(x, y)
+            p.inverse(y, x=xh)
+    plain()
+    torch.cuda.synchronize()
+    e0.record(st)
+    reps = max(1, min(3, args.steps))
+    for _ in range(reps):
+        plain()
+    e1.record(st)
+    e1.synchronize()
+    ms_plain = e0.elapsed_time(e1) / reps
+    bytes_alg = 2 * (ub.envelope_bytes + ub.samples * 4)
+    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
+    line = {"metric": "QTAM fwd+inv Msamples/s, uneven batch in one CUDA graph", "value": round(ub.samples / ms / 1e3, 2),
+            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
+            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "512 segments, 1-32 s, half 4096 Hz / half 16384 Hz, Q {8,16,32} x 128 rows 20-2048 Hz",
+                       "groups": len(ub.groups), "samples": ub.samples, "envelope_bytes": ub.envelope_bytes,
+                       "l2": "inputs+envelopes (1.4 GB) larger than L2"},
+            "path_hbm_frac": round(bytes_alg / (ms * 1e-3) / 1e9 / peak, 4),
+            "per_segment_plain_path": {"value": round(ub.samples / ms_plain / 1e3, 2), "ms_per_step": round(ms_plain, 3),
+                                       "launches": "2 calls per segment, no graph"},
+            "speedup_vs_plain": round(ms_plain / ms, 2), "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_serving(args, local):
+    """Poisson arrivals (200/s) of 3-channel 8 s @ 4096 Hz requests, Q in
+    {8,16,32}, 20 % inverse of row-zeroed envelopes; 40 GB HBM budget."""
+    import torch
+    from paper_2603_29785_gb300 import serve
+    torch.cuda.set_device(local)
+    pool = [serve.make_request(i, 5000 + i) for i in range(256)]
+    arrivals = serve.poisson_arrivals(200.0, args.duration, seed=7)
+    reqs = [serve.Request(i, pool[i % len(pool)].x, pool[i % len(pool)].q, pool[i % len(pool)].kind,
+                          pool[i % len(pool)].row_gain) for i in range(len(arrivals))]
+    ex = serve.GpuExecutor(slots=4, device=local)
+    warm = serve.Server(ex, hbm_budget_bytes=40 * 2**30)
+    serve.run_stream(warm, [serve.Request(-i - 1, r.x, r.q, r.kind, r.row_gain) for i, r in enumerate(pool[:32])],
+                     np.zeros(32), realtime=False)
+    srv = serve.Server(ex, hbm_budget_bytes=40 * 2**30, max_batch_requests=32)
+    st, clk = _clock_wrap(lambda: serve.run_stream(srv, reqs, arrivals), local)
+    line = {"metric": "QTAM serving p50/p99 latency (ms) and Msamples/s", "value": round(st["p99_ms"], 3),
+            "unit": "ms p99", "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "Poisson 200 req/s, 3 x 8 s @ 4096 Hz per request, Q {8,16,32} x 128 rows, "
+                                   "20 % inverse of row-zeroed envelopes", "duration_s": args.duration,
+                       "hbm_budget_gb": 40, "streams": ex.slots, "max_batch_requests": 32},
+            "serving": st, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
+def run_precision(args, local):
+    """Envelope storage FP32 / BF16 / FP16 on the 64 s workload: error against
+    the FP64 oracle (2 segments) and throughput (64 segments)."""
+    import torch
+    from oracle import qtam_oracle as O
+    from paper_2603_29785_gb300 import qtam, tune as qtune
+    torch.cuda.set_device(local)
+    B = args.batch
+    x_host = make_inputs(range(B))
+    g = O.geometry(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"])
+    refs = []
+    for b in range(2):
+        xb = x_host[b].astype(np.float64)
+        Y = O.forward(g, xb)
+        refs.append((Y, O.inverse(g, Y, tau=1e-6)))
+    x = torch.from_numpy(x_host).cuda()
+    out = []
+    for env in ("f32", "bf16", "f16"):
+        p = qtam.Plan(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"],
+                      envelope=env, device=local)
+        qtune.tune(p, B)
+        y = p.forward(x)
+        xh = p.inverse(y)
+        torch.cuda.synchronize()
+        yv = y[:2].float().cpu().numpy() if env != "f32" else y[:2].cpu().numpy()
+        if env != "f32":
+            yv = yv[..., 0] + 1j * yv[..., 1]
+        ef = max(float(np.linalg.norm(yv[b] - refs[b][0]) / np.linalg.norm(refs[b][0])) for b in range(2))
+        er = max(float(np.linalg.norm(xh[b].cpu().numpy() - refs[b][1]) / np.linalg.norm(refs[b][1])) for b in range(2))
+        st = torch.cuda.current_stream()
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for _ in range(3):
+            p.forward(x, y); p.inverse(y, x=xh)
+        e[0].record(st)
+        for _ in range(args.steps):
+            p.forward(x, y); p.inverse(y, x=xh)
+        e[1].record(st)
+        e[1].synchronize()
+        ms = e[0].elapsed_time(e[1]) / args.steps
+        out.append({"envelope": env, "forward_rel_err": ef, "roundtrip_rel_err": er,
+                    "msamples_per_s": round(B * WORKLOAD["N"] / ms / 1e3, 1), "ms_per_step": round(ms, 4),
+                    "envelope_bytes_per_segment": p.info["envelope_bytes_per_segment"]})
+    line = {"metric": "QTAM precision sweep: error vs FP64 oracle and Msamples/s per envelope dtype",
+            "value": out[0]["msamples_per_s"], "unit": UNIT, "n_gpus": 1, "dtype": "f32 compute",
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "segments": B}, "precision": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank)
         return
+    if args.workload == "batched":
+        return run_batched(args, local) if rank == 0 else None
+    if args.workload == "serving":
+        return run_serving(args, local) if rank == 0 else None
+    if args.workload == "precision":
+        return run_precision(args, local) if rank == 0 else None
     run_gpu(args, rank, world, local)
 
 

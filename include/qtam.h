@@ -191,6 +191,40 @@ QTAM_API qtam_status qtam_roundtrip_host(qtam_plan_t plan, const void* x_host, i
                                 void* xhat_host, void* x_dev, void* y_dev, void* xhat_dev,
                                 void* workspace, size_t workspace_bytes, void* stream);
 
+/* Multiply every envelope row by a gain: y[b][p][k][*] *= gain[(b*P + p)*K + k]
+ * (gain: device float array of batch*P*K entries).  Gain 0 zeroes a row --
+ * the masked (row-zeroed) envelopes the inverse accepts; gain 1 leaves the
+ * row untouched.  A pre-processing step for synthesis from a subset of the
+ * tiles (cluster masks, App. C canonical dual of the kept rows). */
+QTAM_API qtam_status qtam_scale_rows(qtam_plan_t plan, void* y, int64_t batch, const float* gain, void* stream);
+
+/* One group of equal-length segments of a batched call: `batch` segments
+ * transformed with `plan`.  forward reads x [batch][N] and writes y
+ * [batch][P][K][M]; inverse reads y and writes x.  Pointers are device
+ * buffers of the plans' device, owned by the caller. */
+typedef struct {
+  qtam_plan_t plan;
+  const void* in;
+  void* out;
+  int64_t batch;
+} qtam_group;
+
+/* Workspace bytes for a batched call over these groups: the largest
+ * single-group workspace (groups run in stream order and share it). */
+QTAM_API qtam_status qtam_batched_workspace_size(const qtam_group* groups, int32_t n_groups, size_t* bytes);
+
+/* Segments of uneven length (one group per plan) in one call: every group's
+ * forward transform (in = x, out = y), enqueued in order on `stream`.  All
+ * plans must live on the same device.  The whole call can be captured into
+ * one CUDA graph (no allocation, no synchronisation inside); make one
+ * uncaptured call first so plane-mask tables and kernel attributes exist. */
+QTAM_API qtam_status qtam_forward_batched(const qtam_group* groups, int32_t n_groups, void* workspace,
+                                          size_t workspace_bytes, void* stream);
+
+/* Batched inverse (in = y, out = x) with the canonical dual of plane_mask. */
+QTAM_API qtam_status qtam_inverse_batched(const qtam_group* groups, int32_t n_groups, uint64_t plane_mask,
+                                          void* workspace, size_t workspace_bytes, void* stream);
+
 /* qtam_forward without a workspace argument, for callers that cannot
  * allocate device memory at call time (real-time loops, host callbacks where
  * a cudaMalloc would stall, plug-ins whose host application owns all device

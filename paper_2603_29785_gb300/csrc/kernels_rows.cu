@@ -317,7 +317,38 @@ const RowVariant kVariants[] = {
 };
 #undef QTAM_V
 
+template <typename V, int E>
+__global__ void k_scale_rows(typename Env<V, E>::S* __restrict__ y, const float* __restrict__ gain, int64_t n_rows,
+                             int M) {
+  // one block-stride loop per row; rows with gain 1 are left untouched
+  for (int64_t r = blockIdx.x; r < n_rows; r += gridDim.x) {
+    const float g = gain[r];
+    if (g == 1.0f) continue;
+    typename Env<V, E>::S* row = y + r * M;
+    for (int i = threadIdx.x; i < M; i += blockDim.x) {
+      V v = Env<V, E>::from(row[i]);
+      v.x *= g;
+      v.y *= g;
+      row[i] = Env<V, E>::to(v);
+    }
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_scale_rows(void* y, int env, const float* gain, int64_t n_rows, int M, cudaStream_t st) {
+  if (n_rows == 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)(n_rows < 65535 ? n_rows : 65535);
+  switch (env) {
+    case ENV_F64: k_scale_rows<double2, ENV_F64><<<blocks, 256, 0, st>>>(static_cast<double2*>(y), gain, n_rows, M); break;
+    case ENV_BF16:
+      k_scale_rows<float2, ENV_BF16><<<blocks, 256, 0, st>>>(static_cast<__nv_bfloat162*>(y), gain, n_rows, M);
+      break;
+    case ENV_F16: k_scale_rows<float2, ENV_F16><<<blocks, 256, 0, st>>>(static_cast<__half2*>(y), gain, n_rows, M); break;
+    default: k_scale_rows<float2, ENV_F32><<<blocks, 256, 0, st>>>(static_cast<float2*>(y), gain, n_rows, M);
+  }
+  return cudaGetLastError();
+}
 
 int row_variant_count() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
 const RowVariant* row_variant(int i) { return (i >= 0 && i < row_variant_count()) ? &kVariants[i] : nullptr; }

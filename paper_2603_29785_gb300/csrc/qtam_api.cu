@@ -848,6 +848,59 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
   return QTAM_OK;
 }
 
+qtam_status qtam_scale_rows(qtam_plan_t pl, void* y, int64_t B, const float* gain, void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK || B == 0) return s;
+  if (!y || !gain) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (!aligned(y, pl->env_size()) || !aligned(gain, 4)) return fail(QTAM_ERR_INVALID_ARG, "misaligned buffer");
+  DeviceGuard g(pl->device);
+  cudaError_t e = launch_scale_rows(y, pl->env, gain, B * (int64_t)pl->P * pl->K, pl->M, static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "scale_rows launch");
+}
+
+qtam_status qtam_batched_workspace_size(const qtam_group* g, int32_t n, size_t* bytes) {
+  if (!bytes || n < 0 || (n > 0 && !g)) return fail(QTAM_ERR_INVALID_ARG, "bad argument");
+  size_t mx = 256;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!g[i].plan || g[i].batch < 0) return fail(QTAM_ERR_INVALID_ARG, "group with NULL plan or negative batch");
+    mx = std::max(mx, ws_bytes(g[i].plan, g[i].batch));
+  }
+  *bytes = mx;
+  return QTAM_OK;
+}
+
+namespace {
+qtam_status check_groups(const qtam_group* g, int32_t n, size_t wsb) {
+  if (n < 0 || (n > 0 && !g)) return fail(QTAM_ERR_INVALID_ARG, "bad group list");
+  int dev = -2;
+  for (int32_t i = 0; i < n; ++i) {
+    qtam_status s = common_checks(g[i].plan, g[i].batch);
+    if (s != QTAM_OK) return s;
+    if (dev != -2 && g[i].plan->device != dev) return fail(QTAM_ERR_INVALID_ARG, "groups on different devices");
+    dev = g[i].plan->device;
+    if (g[i].batch > 0 && (!g[i].in || !g[i].out)) return fail(QTAM_ERR_INVALID_ARG, "group with NULL buffer");
+    if (wsb < ws_bytes(g[i].plan, g[i].batch)) return fail(QTAM_ERR_WORKSPACE, "workspace too small for a group");
+  }
+  return QTAM_OK;
+}
+}  // namespace
+
+qtam_status qtam_forward_batched(const qtam_group* g, int32_t n, void* ws, size_t wsb, void* stream) {
+  qtam_status s = check_groups(g, n, wsb);
+  if (s != QTAM_OK) return s;
+  for (int32_t i = 0; i < n; ++i)
+    if ((s = qtam_forward(g[i].plan, g[i].in, g[i].batch, g[i].out, ws, wsb, stream)) != QTAM_OK) return s;
+  return QTAM_OK;
+}
+
+qtam_status qtam_inverse_batched(const qtam_group* g, int32_t n, uint64_t mask, void* ws, size_t wsb, void* stream) {
+  qtam_status s = check_groups(g, n, wsb);
+  if (s != QTAM_OK) return s;
+  for (int32_t i = 0; i < n; ++i)
+    if ((s = qtam_inverse(g[i].plan, g[i].in, g[i].batch, mask, g[i].out, ws, wsb, stream)) != QTAM_OK) return s;
+  return QTAM_OK;
+}
+
 qtam_status qtam_destroy(qtam_plan_t pl) {
   free_plan(pl);
   return QTAM_OK;

@@ -73,6 +73,8 @@ struct RowVariant {
   RowInvFn inv[4];
 };
 int row_variant_count();
+// y[r][*] *= gain[r] for r < n_rows (device gains), envelope storage kind env
+cudaError_t launch_scale_rows(void* y, int env, const float* gain, int64_t n_rows, int M, cudaStream_t st);
 const RowVariant* row_variant(int i);   // nullptr when out of range
 
 // ---- launchers (kernels_long.cu) ----

@@ -47,6 +47,11 @@ class qtam_plan_desc(ctypes.Structure):
     ]
 
 
+class qtam_group(ctypes.Structure):
+    _fields_ = [("plan", ctypes.c_void_p), ("input", ctypes.c_void_p), ("output", ctypes.c_void_p),
+                ("batch", ctypes.c_int64)]
+
+
 class qtam_plan_info_t(ctypes.Structure):
     _fields_ = [
         ("length", ctypes.c_int64), ("n_bins", ctypes.c_int64), ("n_planes", ctypes.c_int32),
@@ -83,6 +88,10 @@ SIGNATURES = {
     "qtam_stage_synthesize": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P, _SZ, _P]),
     "qtam_roundtrip_host": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P, _P, _P, _P, _SZ, _P]),
     "qtam_forward_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "qtam_scale_rows": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "qtam_batched_workspace_size": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_SZ)]),
+    "qtam_forward_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _SZ, _P]),
+    "qtam_inverse_batched": (ctypes.c_int, [_P, ctypes.c_int32, _U64, _P, _SZ, _P]),
     "qtam_destroy": (ctypes.c_int, [_P]),
     "qtam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qtam_last_error": (ctypes.c_char_p, []),
@@ -251,6 +260,40 @@ def qtam_forward_noalloc(plan, x, batch, y, stream=None):
     _check(lib().qtam_forward_noalloc(plan, _ptr(x), int(batch), _ptr(y), _stream(stream)))
 
 
+def qtam_scale_rows(plan, y, batch, gain, stream=None):
+    _check(lib().qtam_scale_rows(plan, _ptr(y), int(batch), _ptr(gain), _stream(stream)))
+
+
+def make_groups(groups) -> ctypes.Array:
+    """groups: iterable of (plan handle, input tensor/pointer, output tensor/pointer, batch)."""
+    groups = list(groups)
+    arr = (qtam_group * max(1, len(groups)))()
+    for i, (plan, inp, out, batch) in enumerate(groups):
+        arr[i].plan = plan
+        arr[i].input = _ptr(inp)
+        arr[i].output = _ptr(out)
+        arr[i].batch = int(batch)
+    return arr, len(groups)
+
+
+def qtam_batched_workspace_size(groups) -> int:
+    arr, n = make_groups(groups)
+    s = _SZ()
+    _check(lib().qtam_batched_workspace_size(arr, n, ctypes.byref(s)))
+    return s.value
+
+
+def qtam_forward_batched(groups, workspace, workspace_bytes, stream=None):
+    arr, n = make_groups(groups)
+    _check(lib().qtam_forward_batched(arr, n, _ptr(workspace), int(workspace_bytes), _stream(stream)))
+
+
+def qtam_inverse_batched(groups, plane_mask, workspace, workspace_bytes, stream=None):
+    arr, n = make_groups(groups)
+    _check(lib().qtam_inverse_batched(arr, n, int(plane_mask), _ptr(workspace), int(workspace_bytes),
+                                      _stream(stream)))
+
+
 def qtam_destroy(plan):
     if plan:
         lib().qtam_destroy(plan)
@@ -388,6 +431,14 @@ class Plan:
         ws, wsb = self.workspace(B)
         qtam_inverse(self.handle, y, B, plane_mask, x, ws, wsb, stream)
         return x
+
+    def scale_rows(self, y, gain, stream=None):
+        """y[b, p, k, :] *= gain[b, p, k] in place (gain: CUDA float32 [batch, P, K])."""
+        self._check_y(y)
+        B = y.shape[0]
+        _require(gain, (B, self.P, self.K), (__import__("torch").float32,), self.device, "gain")
+        qtam_scale_rows(self.handle, y, B, gain, stream)
+        return y
 
     def spectrum(self, x, stream=None):
         import torch

@@ -124,3 +124,16 @@ def test_binding_rejects_mismatched_tensors():
         p.inverse(torch.zeros((1, p.P, p.K, p.M + 1), dtype=torch.complex64))
     with pytest.raises(ValueError):
         p.synthesize(torch.zeros((1, p.Nr), dtype=torch.complex128))
+
+
+def test_batched_workspace_is_largest_group():
+    a = qtam.Plan(4096.0, 4096, (8.0, 16.0, 32.0), 20.0, 2048.0, 128, device=-1)
+    b = qtam.Plan(4096.0, 32768, (8.0, 16.0, 32.0), 20.0, 2048.0, 128, device=-1)
+    ga = (a.handle, 0, 0, 7)
+    gb = (b.handle, 0, 0, 3)
+    want = max(qtam.qtam_workspace_size(a.handle, 7), qtam.qtam_workspace_size(b.handle, 3))
+    assert qtam.qtam_batched_workspace_size([ga, gb]) == want
+    with pytest.raises(qtam.QtamError):
+        qtam.qtam_forward_batched([ga, gb], 0, want, stream=0)   # host-only plans cannot run
+    with pytest.raises(qtam.QtamError):
+        qtam.qtam_batched_workspace_size([(a.handle, 0, 0, -1)])
