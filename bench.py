@@ -44,11 +44,28 @@ def parse():
     ap.add_argument("--cpu-sample-segments", type=int, default=4)
     ap.add_argument("--variant", type=int, default=None,
                     help="row-kernel variant id (default: chosen by the autotuner)")
-    ap.add_argument("--workload", default="64s", choices=["64s", "batched", "serving", "precision"],
+    ap.add_argument("--workload", default="64s", choices=["64s", "batched", "serving", "precision", "latency"],
                     help="64s: the headline workload (default); batched: 512 uneven segments in one graph; "
                          "serving: Poisson request stream; precision: envelope dtype sweep")
     ap.add_argument("--duration", type=float, default=60.0, help="seconds of arrivals for --workload serving")
     return ap.parse_args()
+
+
+def rank_seeds(rank: int, per_rank: int):
+    """Distinct input seeds per rank: each rank transforms its own segments
+    (weak scaling, replicas; no data crosses ranks)."""
+    return [rank * per_rank + i for i in range(per_rank)]
+
+
+def reduce_max(value: float, dist, device=None) -> float:
+    """Max of a per-rank value over all ranks (the job time is the slowest
+    rank's); identity without a process group."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def dist_env():
@@ -145,6 +162,22 @@ def run_reference(args, rank):
     print(json.dumps(line), flush=True)
 
 
+def measured_traffic(kernel: str):
+    """DRAM bytes per full-size launch from the committed ncu capture, or None
+    when the kernel sources changed since the counters were taken."""
+    import hashlib
+    try:
+        tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
+        h = hashlib.sha256()
+        for f in ("kernels_rows.cu", "fft_static.cuh", "fft_core.cuh", "qtam_internal.h"):
+            h.update(open(os.path.join(ROOT, "paper_2603_29785_gb300", "csrc", f), "rb").read())
+        if h.hexdigest() != tr.get("source_sha256"):
+            return None
+        return tr.get(kernel, {}).get("bytes_per_launch_full")
+    except (OSError, ValueError):
+        return None
+
+
 # ---------------------------------------------------------------------------- GPU arm
 def cpu_baseline_leg(p, x_host, xh_gpu, y_gpu, nseg):
     """Oracle on a bounded sample (nseg segments): timing + GPU-vs-oracle error."""
@@ -180,7 +213,7 @@ def run_gpu(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B = args.batch
-    seeds = [rank * B + i for i in range(B)]
+    seeds = rank_seeds(rank, B)
     x_host = make_inputs(seeds)
     p = qtam.Plan(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"],
                   device=local)
@@ -238,11 +271,7 @@ def run_gpu(args, rank, world, local):
     if dist is not None:
         dist.barrier()
     clk = clocks.stop()
-    ms_per_step = total_ms / args.steps
-    if dist is not None:
-        tt = torch.tensor([ms_per_step], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms_per_step = float(tt.item())
+    ms_per_step = reduce_max(total_ms / args.steps, dist, dev)
     samples_per_step = world * B * N
     value = samples_per_step / (ms_per_step * 1e-3) / 1e6
 
@@ -256,11 +285,7 @@ def run_gpu(args, rank, world, local):
     e2e_steps = max(3, args.steps // 2)
     for _ in range(e2e_steps):
         qtam.qtam_roundtrip_host(h, x_pin, B, 0, xh_pin, x, y, xh, ws, wsb, st)
-    e2e_s = (time.perf_counter() - t0) / e2e_steps
-    if dist is not None:
-        tt = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        e2e_s = float(tt.item())
+    e2e_s = reduce_max((time.perf_counter() - t0) / e2e_steps, dist, dev)
     e2e = {"value": samples_per_step / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": B * N * 4,
            "d2h_bytes_per_step": B * N * 4, "ms_per_step": e2e_s * 1e3}
 
@@ -283,13 +308,7 @@ def run_gpu(args, rank, world, local):
         kernels[nm] = {"ms": round(float(t), 4), "alg_bytes": int(b), "GB_s": round(b / (t * 1e-3) / 1e9, 1)}
     dom = int(np.argmax(stage_avg_ms[1:3])) + 1
     achieved = stage_bytes[dom] / (stage_avg_ms[dom] * 1e-3) / 1e9
-    traffic_path = os.path.join(ROOT, "profiles", "traffic.json")
-    traffic = None
-    try:
-        tr = json.load(open(traffic_path))
-        traffic = tr.get(["", "k_rows_forward", "k_rows_inverse"][dom], {}).get("bytes_per_launch_full")
-    except (OSError, ValueError):
-        pass
+    traffic = measured_traffic(["", "k_rows_forward", "k_rows_inverse"][dom])
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved / hbm_peak, 4), "traffic": traffic, "kernel": stage_names[dom],
                 "peak_source": peak_src}
@@ -469,6 +488,42 @@ def run_precision(args, local):
     print(json.dumps(line), flush=True)
 
 
+def run_latency(args, local):
+    """Single-segment forward+inverse latency: the 4 s FP64 case (white noise +
+    sine-Gaussian, Q=8, 64 rows 20-1024 Hz) and one 64 s FP32 segment."""
+    import torch
+    from paper_2603_29785_gb300 import qtam, synth, tune as qtune
+    torch.cuda.set_device(local)
+    cases = [("4 s @ 4096 Hz, Q=8, 64 rows, FP64", dict(fs=4096.0, N=16384, qs=(8.0,), fmin=20.0, fmax=1024.0, K=64),
+              "f64", synth.white_sine_gaussian_segment(0).astype(np.float64)),
+             ("64 s @ 4096 Hz, Q {4..64}, 128 rows, FP32", WORKLOAD, "f32", make_inputs([0])[0])]
+    res = []
+    st = torch.cuda.current_stream()
+    for name, w, dt, xn in cases:
+        p = qtam.Plan(w["fs"], w["N"], w["qs"], w["fmin"], w["fmax"], w["K"], compute=dt, device=local)
+        if dt == "f32":
+            qtune.tune(p, 1)
+        x = torch.from_numpy(xn[None]).cuda()
+        y = p.forward(x)
+        xh = p.inverse(y)
+        ts = []
+        for i in range(args.warmup + args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(st)
+            p.forward(x, y)
+            p.inverse(y, x=xh)
+            e1.record(st)
+            e1.synchronize()
+            if i >= args.warmup:
+                ts.append(e0.elapsed_time(e1))
+        res.append({"case": name, "dtype": dt, "median_ms": round(float(np.median(ts)), 4),
+                    "p99_ms": round(float(np.percentile(ts, 99)), 4), "M": p.M})
+    line = {"metric": "QTAM single-segment fwd+inv latency", "value": res[0]["median_ms"], "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "data": "synthetic", "steps": args.steps, "warmup": args.warmup,
+            "latency": res}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -481,6 +536,8 @@ def main():
         return run_serving(args, local) if rank == 0 else None
     if args.workload == "precision":
         return run_precision(args, local) if rank == 0 else None
+    if args.workload == "latency":
+        return run_latency(args, local) if rank == 0 else None
     run_gpu(args, rank, world, local)
 
 
