@@ -51,11 +51,13 @@ template <typename V> struct LoadColumns {
   const V* zs; int n2; int c0;
   __device__ __forceinline__ V get(int b, int m1) const { return zs[(int64_t)m1 * n2 + c0 + b]; }
 };
+// tw4[k1 * n2 + c] = w_n^(c k1): the four-step twiddles in the layout of U,
+// so a warp's loads are as contiguous as its stores.
 template <typename V> struct StoreColumnsTwiddled {
-  V* Us; const V* twn; int n2; int c0;
+  V* Us; const V* tw4; int n2; int c0;
   __device__ __forceinline__ void put(int b, int k1, V v) const {
-    const int c = c0 + b;
-    Us[(int64_t)k1 * n2 + c] = cmul(v, __ldg(&twn[(int64_t)c * k1]));
+    const int64_t e = (int64_t)k1 * n2 + c0 + b;
+    Us[e] = cmul(v, __ldg(&tw4[e]));
   }
 };
 template <typename V> struct LoadRows {
@@ -69,7 +71,7 @@ template <typename V> struct StoreRowsTransposed {
 
 template <class Eng, typename T>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_col_forward(Eng eng, int n, int n2, const cplx<T>* __restrict__ z,
-                                                          cplx<T>* __restrict__ U, const cplx<T>* __restrict__ twn,
+                                                          cplx<T>* __restrict__ U, const cplx<T>* __restrict__ tw4,
                                                           const cplx<T>* __restrict__ ftw) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -77,7 +79,7 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_col_forward(Eng eng, int
   const int64_t seg = blockIdx.y;
   const int c0 = blockIdx.x << eng.nb_shift();
   LoadColumns<V> ld{z + seg * n, n2, c0};
-  StoreColumnsTwiddled<V> stv{U + seg * n, twn, n2, c0};
+  StoreColumnsTwiddled<V> stv{U + seg * n, tw4, n2, c0};
   eng.template run<-1>(sm, ftw, n / eng.m(), ld, stv);
 }
 
@@ -101,57 +103,86 @@ template <typename V> __device__ __forceinline__ V wN(const V* twN, int n, int k
   return mk<V>(-t.x, t.y);
 }
 
+constexpr int kUntanglePairs = 4;   // (k, n-k) pairs per thread, for memory-level parallelism
+
 template <typename T>
 __global__ void k_untangle_forward(int n, const cplx<T>* __restrict__ Z, cplx<T>* __restrict__ X,
                                    const cplx<T>* __restrict__ twN) {
   using V = cplx<T>;
   const int64_t seg = blockIdx.y;
-  const int k = blockIdx.x * blockDim.x + threadIdx.x;
-  if (k > (n >> 1)) return;
   const V* Zs = Z + seg * n;
   V* Xs = X + seg * (int64_t)(n + 1);
-  const int kk = n - k;                     // partner bin, in [n/2, n]
-  const V zk = Zs[k];
-  const V zm = Zs[kk == n ? 0 : kk];
   const T half = (T)0.5;
-  {
-    const V a = zk, b = cconj(zm);
-    const V s = a + b, d = a - b;
-    const V t = cmul(__ldg(&twN[k]), d);    // w^k (a - b)
-    Xs[k] = mk<V>(half * (s.x + t.y), half * (s.y - t.x));   // s/2 - (i/2) t
-  }
-  if (kk != k) {
-    const V a = zm, b = cconj(zk);
-    const V s = a + b, d = a - b;
-    const V t = cmul(wN(twN, n, kk), d);
-    Xs[kk] = mk<V>(half * (s.x + t.y), half * (s.y - t.x));
+  const int base = blockIdx.x * blockDim.x * kUntanglePairs + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kUntanglePairs; ++u) {
+    const int k = base + u * blockDim.x;
+    if (k > (n >> 1)) break;
+    const int kk = n - k;                     // partner bin, in [n/2, n]
+    const V zk = Zs[k];
+    const V zm = Zs[kk == n ? 0 : kk];
+    {
+      const V a = zk, b = cconj(zm);
+      const V s = a + b, d = a - b;
+      const V t = cmul(__ldg(&twN[k]), d);    // w^k (a - b)
+      Xs[k] = mk<V>(half * (s.x + t.y), half * (s.y - t.x));   // s/2 - (i/2) t
+    }
+    if (kk != k) {
+      const V a = zm, b = cconj(zk);
+      const V s = a + b, d = a - b;
+      const V t = cmul(wN(twN, n, kk), d);
+      Xs[kk] = mk<V>(half * (s.x + t.y), half * (s.y - t.x));
+    }
   }
 }
 
-// Inverse row pass input: Zi[k] = scale (E[k] + i O[k]) with
-//   E = (Xh[k] + conj Xh[n-k]) / 2,  O = (Xh[k] - conj Xh[n-k]) / 2 * w_N^(-k),
-//   Xh = A * (1/P), DC and Nyquist taken real.
-template <typename T> struct LoadUntangleInverse {
+// Inverse untangle with the dual-frame normaliser: for the pair (k, n-k),
+//   Xh = A * (1/P) (DC and Nyquist taken real),
+//   Zi[k] = scale (E[k] + i O[k]),  E = (Xh[k] + conj Xh[n-k]) / 2,
+//   O = (Xh[k] - conj Xh[n-k]) / 2 * w_N^(-k),
+// written in natural order; coalesced reads and writes, pairs per thread.
+template <typename T>
+__device__ __forceinline__ cplx<T> zi_value(cplx<T> xk, cplx<T> xm, cplx<T> wk, T hs) {
   using V = cplx<T>;
-  const V* As; const T* invP; const V* twN; int n; int n1; int r0; T scale;
-  __device__ __forceinline__ V get(int b, int k2) const {
-    const int k = r0 + b + n1 * k2;          // 0 <= k < n
-    const int kk = n - k;                    // 1 <= kk <= n
+  const V e = xk + cconj(xm);
+  const V o = cmul(xk - cconj(xm), cconj(wk));
+  return mk<V>(hs * (e.x - o.y), hs * (e.y + o.x));    // scale/2 (e + i o)
+}
+
+template <typename T>
+__global__ void k_untangle_inverse(int n, const cplx<T>* __restrict__ A, const T* __restrict__ invP,
+                                   cplx<T>* __restrict__ Zi, const cplx<T>* __restrict__ twN, T scale) {
+  using V = cplx<T>;
+  const int64_t seg = blockIdx.y;
+  const V* As = A + seg * (int64_t)(n + 1);
+  V* Zs = Zi + seg * n;
+  const T hs = (T)0.5 * scale;
+  const int base = blockIdx.x * blockDim.x * kUntanglePairs + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kUntanglePairs; ++u) {
+    const int k = base + u * blockDim.x;
+    if (k > (n >> 1)) break;
+    const int kk = n - k;                     // in [n/2, n]
     V xk = cscale(As[k], __ldg(&invP[k]));
     V xm = cscale(As[kk], __ldg(&invP[kk]));
     if (k == 0) xk.y = (T)0;
     if (kk == n) xm.y = (T)0;
-    const V e = xk + cconj(xm);
-    const V o = cmul(xk - cconj(xm), cconj(wN(twN, n, k)));
-    const T hs = (T)0.5 * scale;
-    return mk<V>(hs * (e.x - o.y), hs * (e.y + o.x));    // scale/2 (e + i o)
+    const V wk = __ldg(&twN[k]);
+    Zs[k] = zi_value<T>(xk, xm, wk, hs);
+    if (kk != k && kk != n) Zs[kk] = zi_value<T>(xm, xk, mk<V>(-wk.x, wk.y), hs);   // w^(n-k) = -conj(w^k)
   }
+}
+
+// row pass of the inverse: rows k1 of Zi, read with stride n1
+template <typename V> struct LoadRowsTransposed {
+  const V* Zs; int n1; int r0;
+  __device__ __forceinline__ V get(int b, int k2) const { return Zs[(int64_t)k2 * n1 + r0 + b]; }
 };
 template <typename V> struct StoreRowsTwiddledConj {
-  V* Vs; const V* twn; int n2; int r0;
+  V* Vs; const V* tw4; int n2; int r0;
   __device__ __forceinline__ void put(int b, int m2, V v) const {
-    const int r = r0 + b;
-    Vs[(int64_t)r * n2 + m2] = cmul(v, cconj(__ldg(&twn[(int64_t)r * m2])));
+    const int64_t e = (int64_t)(r0 + b) * n2 + m2;
+    Vs[e] = cmul(v, cconj(__ldg(&tw4[e])));
   }
 };
 template <typename V> struct StoreColumns {
@@ -160,18 +191,16 @@ template <typename V> struct StoreColumns {
 };
 
 template <class Eng, typename T>
-__global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_row_inverse(Eng eng, int n, int n1, const cplx<T>* __restrict__ A,
-                                                          const T* __restrict__ invP, cplx<T>* __restrict__ Vb,
-                                                          const cplx<T>* __restrict__ twn,
-                                                          const cplx<T>* __restrict__ twN, T scale,
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB) k_row_inverse(Eng eng, int n, int n1, const cplx<T>* __restrict__ Zi,
+                                                          cplx<T>* __restrict__ Vb, const cplx<T>* __restrict__ tw4,
                                                           const cplx<T>* __restrict__ ftw) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
   const int64_t seg = blockIdx.y;
   const int r0 = blockIdx.x << eng.nb_shift();
-  LoadUntangleInverse<T> ld{A + seg * (int64_t)(n + 1), invP, twN, n, n1, r0, scale};
-  StoreRowsTwiddledConj<V> stv{Vb + seg * n, twn, eng.m(), r0};
+  LoadRowsTransposed<V> ld{Zi + seg * n, n1, r0};
+  StoreRowsTwiddledConj<V> stv{Vb + seg * n, tw4, eng.m(), r0};
   eng.template run<+1>(sm, ftw, n / eng.m(), ld, stv);
 }
 
@@ -255,36 +284,40 @@ bool long_static_radices(int m, int nbs, int* r, int* nst) {
 template <typename T>
 cudaError_t launch_spectrum(const LongCfg& c, const cplx<T>* z, cplx<T>* U, cplx<T>* Z, cplx<T>* X, int64_t B,
                             const cplx<T>* twn, const cplx<T>* twN, cudaStream_t st) {
+  const cplx<T>* tw4 = static_cast<const cplx<T>*>(c.tw4);
   for (int64_t s0 = 0; s0 < B; s0 += kMaxGridY) {
     const int64_t nb = (B - s0) < kMaxGridY ? (B - s0) : kMaxGridY;
     const int64_t off = s0 * c.n;
     with_engine<T>(c.rp1, c.col_nbs, 4, c.col_smem, c.stw_col, twn, [&](auto eng, size_t smem, const cplx<T>* ftw) {
       using E = decltype(eng);
       dim3 g(c.n2 >> c.col_nbs, (unsigned)nb);
-      launch_pass(k_col_forward<E, T>, eng, smem, g, st, c.n, c.n2, z + off, U + off, twn, ftw);
+      launch_pass(k_col_forward<E, T>, eng, smem, g, st, c.n, c.n2, z + off, U + off, tw4, ftw);
     });
     with_engine<T>(c.rp2, c.row_nbs, 2, c.row_smem, c.stw_row, twn, [&](auto eng, size_t smem, const cplx<T>* ftw) {
       using E = decltype(eng);
       dim3 g(c.n1 >> c.row_nbs, (unsigned)nb);
       launch_pass(k_row_forward<E, T>, eng, smem, g, st, c.n, c.n1, (const cplx<T>*)(U + off), Z + off, ftw);
     });
-    dim3 g3((unsigned)((c.n / 2 + 1 + 255) / 256), (unsigned)nb);
+    dim3 g3((unsigned)((c.n / 2 + 1 + 256 * kUntanglePairs - 1) / (256 * kUntanglePairs)), (unsigned)nb);
     k_untangle_forward<T><<<g3, 256, 0, st>>>(c.n, Z + off, X + s0 * (int64_t)(c.n + 1), twN);
   }
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t launch_synthesis(const LongCfg& c, const cplx<T>* A, const T* invP, cplx<T>* Vb, cplx<T>* xout, int64_t B,
-                             const cplx<T>* twn, const cplx<T>* twN, cudaStream_t st) {
+cudaError_t launch_synthesis(const LongCfg& c, const cplx<T>* A, const T* invP, cplx<T>* Zi, cplx<T>* Vb,
+                             cplx<T>* xout, int64_t B, const cplx<T>* twn, const cplx<T>* twN, cudaStream_t st) {
+  const cplx<T>* tw4 = static_cast<const cplx<T>*>(c.tw4);
   for (int64_t s0 = 0; s0 < B; s0 += kMaxGridY) {
     const int64_t nb = (B - s0) < kMaxGridY ? (B - s0) : kMaxGridY;
     const int64_t off = s0 * c.n;
+    dim3 g0((unsigned)((c.n / 2 + 1 + 256 * kUntanglePairs - 1) / (256 * kUntanglePairs)), (unsigned)nb);
+    k_untangle_inverse<T><<<g0, 256, 0, st>>>(c.n, A + s0 * (int64_t)(c.n + 1), invP, Zi + off, twN,
+                                              (T)1 / (T)c.n);
     with_engine<T>(c.rp2, c.row_nbs, 2, c.row_smem, c.stw_row, twn, [&](auto eng, size_t smem, const cplx<T>* ftw) {
       using E = decltype(eng);
       dim3 g(c.n1 >> c.row_nbs, (unsigned)nb);
-      launch_pass(k_row_inverse<E, T>, eng, smem, g, st, c.n, c.n1, A + s0 * (int64_t)(c.n + 1), invP, Vb + off,
-                  twn, twN, (T)1 / (T)c.n, ftw);
+      launch_pass(k_row_inverse<E, T>, eng, smem, g, st, c.n, c.n1, (const cplx<T>*)(Zi + off), Vb + off, tw4, ftw);
     });
     with_engine<T>(c.rp1, c.col_nbs, 4, c.col_smem, c.stw_col, twn, [&](auto eng, size_t smem, const cplx<T>* ftw) {
       using E = decltype(eng);
@@ -299,9 +332,9 @@ template cudaError_t launch_spectrum<float>(const LongCfg&, const float2*, float
                                             const float2*, const float2*, cudaStream_t);
 template cudaError_t launch_spectrum<double>(const LongCfg&, const double2*, double2*, double2*, double2*, int64_t,
                                              const double2*, const double2*, cudaStream_t);
-template cudaError_t launch_synthesis<float>(const LongCfg&, const float2*, const float*, float2*, float2*, int64_t,
-                                             const float2*, const float2*, cudaStream_t);
-template cudaError_t launch_synthesis<double>(const LongCfg&, const double2*, const double*, double2*, double2*, int64_t,
-                                              const double2*, const double2*, cudaStream_t);
+template cudaError_t launch_synthesis<float>(const LongCfg&, const float2*, const float*, float2*, float2*, float2*,
+                                             int64_t, const float2*, const float2*, cudaStream_t);
+template cudaError_t launch_synthesis<double>(const LongCfg&, const double2*, const double*, double2*, double2*,
+                                              double2*, int64_t, const double2*, const double2*, cudaStream_t);
 
 }  // namespace qtam

@@ -149,6 +149,7 @@ struct qtam_plan_s {
   void* d_twM = nullptr;
   void* d_twn = nullptr;
   void* d_twN = nullptr;
+  void* d_tw4 = nullptr;
   size_t device_bytes = 0;
   std::map<int, void*> variant_tw;   // stage twiddle tables per row-kernel variant
   void* d_stw_col = nullptr;
@@ -268,15 +269,16 @@ bool choose_long(int64_t n, bool dbl, LongCfg& lc) {
     const int64_t n2 = n / n1;
     RadixPlan r1, r2;
     if (!make_radix_plan((int)n1, r1) || !make_radix_plan((int)n2, r2)) continue;
-    int cn = dbl ? 3 : 4, rn = dbl ? 1 : 2;
-    while (cn > 0 && n2 % (1 << cn)) --cn;
-    while (rn > 0 && n1 % (1 << rn)) --rn;
+    const int cmax = dbl ? 3 : 4, rmax = dbl ? 1 : 2;
+    int cn = cmax, rn = rmax;
+    while (cn > 0 && (n2 % (1 << cn) || threads_for(r1, cn) > kMaxThreads || smem_for(r1, cn, elem) > (size_t)kMaxSmem)) --cn;
+    while (rn > 0 && (n1 % (1 << rn) || threads_for(r2, rn) > kMaxThreads || smem_for(r2, rn, elem) > (size_t)kMaxSmem)) --rn;
     const int t1 = threads_for(r1, cn), t2 = threads_for(r2, rn);
     const size_t s1 = smem_for(r1, cn, elem), s2 = smem_for(r2, rn, elem);
     if (t1 > kMaxThreads || t2 > kMaxThreads || s1 > (size_t)kMaxSmem || s2 > (size_t)kMaxSmem) continue;
     // prefer balanced splits and full-width column groups
-    const double score = std::fabs(std::log2((double)n1) - std::log2((double)n2) + 1.0) + (cn < (dbl ? 3 : 4) ? 4 : 0) +
-                         (rn < (dbl ? 1 : 2) ? 2 : 0);
+    const double score = std::fabs(std::log2((double)n1) - std::log2((double)n2) + 1.0) + (cmax - cn) * 2.0 +
+                         (rmax - rn) * 1.0;
     if (score < best) {
       best = score;
       found = true;
@@ -318,6 +320,20 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
   if ((s = upload(&pl->d_twn, tw.data(), tw.size() * sizeof(T), tot)) != QTAM_OK) return s;
   fill_twiddles(tw, pl->N, pl->n / 2 + 1);
   if ((s = upload(&pl->d_twN, tw.data(), tw.size() * sizeof(T), tot)) != QTAM_OK) return s;
+  {  // four-step twiddles in [k1][c] layout: w_n^(k1 c), exponent reduced mod n in integers
+    const int64_t n1 = pl->lc.n1, n2 = pl->lc.n2;
+    std::vector<T> t4(2 * (size_t)pl->n);
+    const double two_pi = 6.283185307179586476925286766559;
+    for (int64_t k1 = 0; k1 < n1; ++k1)
+      for (int64_t c = 0; c < n2; ++c) {
+        const int64_t e = (k1 * c) % pl->n;
+        const double ang = two_pi * (double)e / (double)pl->n;
+        t4[2 * (k1 * n2 + c)] = (T)std::cos(ang);
+        t4[2 * (k1 * n2 + c) + 1] = (T)(-std::sin(ang));
+      }
+    if ((s = upload(&pl->d_tw4, t4.data(), t4.size() * sizeof(T), tot)) != QTAM_OK) return s;
+    pl->lc.tw4 = pl->d_tw4;
+  }
   std::vector<RowDev<T>> rows(pl->P * pl->K);
   const double sMN = std::sqrt((double)pl->M * (double)pl->N), sNM = std::sqrt((double)pl->N / (double)pl->M);
   for (size_t r = 0; r < rows.size(); ++r) {
@@ -363,6 +379,7 @@ void free_plan(qtam_plan_s* pl) {
     cudaFree(pl->d_twM);
     cudaFree(pl->d_twn);
     cudaFree(pl->d_twN);
+    cudaFree(pl->d_tw4);
     cudaFree(pl->d_stw_col);
     cudaFree(pl->d_stw_row);
     for (auto& kv : pl->variant_tw) cudaFree(kv.second);
@@ -438,9 +455,10 @@ qtam_status run_synthesize(qtam_plan_s* pl, const void* A, int64_t B, const Mask
                            cudaStream_t st) {
   using V = cplx<T>;
   Regions rg = split_ws(pl, ws, B);
+  // Zi in region 1, V in region 0 (region 0 may hold A, which the untangle consumes first)
   cudaError_t e = launch_synthesis<T>(pl->lc, static_cast<const V*>(A), static_cast<const T*>(me->invP),
-                                      static_cast<V*>(rg.r1), static_cast<V*>(x), B, static_cast<const V*>(pl->d_twn),
-                                      static_cast<const V*>(pl->d_twN), st);
+                                      static_cast<V*>(rg.r1), static_cast<V*>(rg.r0), static_cast<V*>(x), B,
+                                      static_cast<const V*>(pl->d_twn), static_cast<const V*>(pl->d_twN), st);
   return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "synthesis launch");
 }
 

@@ -36,6 +36,7 @@ template <typename T> struct RowDev {
 struct LongCfg {
   const void* stw_col = nullptr;   // stage twiddle tables of the static column engine (or null)
   const void* stw_row = nullptr;   // ... of the static row engine
+  const void* tw4 = nullptr;       // [n1][n2] four-step twiddles w_n^(k1 c), layout of the column-pass output
   int n;        // N / 2
   int n1, n2;   // column length n1 (stride n2), row length n2
   int col_nbs;  // log2 of columns per column-pass block
@@ -82,10 +83,11 @@ const RowVariant* row_variant(int i);   // nullptr when out of range
 template <typename T>
 cudaError_t launch_spectrum(const LongCfg& c, const cplx<T>* z, cplx<T>* U, cplx<T>* Z, cplx<T>* X, int64_t B,
                             const cplx<T>* twn, const cplx<T>* twN, cudaStream_t st);
-// A: [B][n+1] accumulated spectrum; invP: [n+1]; V: [B][n] scratch; xout: [B][n] complex view of the output
+// A: [B][n+1] accumulated spectrum; invP: [n+1]; Zi, V: [B][n] scratch (V may alias A's
+// buffer: A is consumed before V is written); xout: [B][n] complex view of the output
 template <typename T>
-cudaError_t launch_synthesis(const LongCfg& c, const cplx<T>* A, const T* invP, cplx<T>* V, cplx<T>* xout, int64_t B,
-                             const cplx<T>* twn, const cplx<T>* twN, cudaStream_t st);
+cudaError_t launch_synthesis(const LongCfg& c, const cplx<T>* A, const T* invP, cplx<T>* Zi, cplx<T>* V,
+                             cplx<T>* xout, int64_t B, const cplx<T>* twn, const cplx<T>* twN, cudaStream_t st);
 
 // ---- launchers (kernels_rows.cu) ----
 // X: [B][Nr] spectrum -> y: [B][R][M] envelopes (R = P*K rows)
