@@ -189,14 +189,50 @@ template <int R1, int R2, int S> struct DftComposite {
     }
   }
 };
-template <int S> struct Dft<6, S> : DftComposite<2, 3, S> {};
+// Prime-factor (Good-Thomas) DFT for R = R1 R2 with gcd(R1, R2) = 1: the
+// input index n = (R2 n1 + R1 n2) mod R and output index
+// k = (R2 (R2^-1 mod R1) k1 + R1 (R1^-1 mod R2) k2) mod R turn the DFT into
+// R2 DFTs of length R1 followed by R1 DFTs of length R2 with no twiddles.
+__host__ __device__ constexpr int inv_mod(int a, int m) {
+  for (int x = 1; x < m; ++x)
+    if ((a * x) % m == 1) return x;
+  return 1;
+}
+template <int R1, int R2, int S> struct DftPFA {
+  static constexpr int R = R1 * R2;
+  static constexpr int E1 = R2 * inv_mod(R2 % R1, R1);
+  static constexpr int E2 = R1 * inv_mod(R1 % R2, R2);
+  template <typename V> __device__ __forceinline__ static void run(V* a) {
+    V b[R];
+#pragma unroll
+    for (int n2 = 0; n2 < R2; ++n2) {
+      V col[R1];
+#pragma unroll
+      for (int n1 = 0; n1 < R1; ++n1) col[n1] = a[(R2 * n1 + R1 * n2) % R];
+      Dft<R1, S>::run(col);
+#pragma unroll
+      for (int k1 = 0; k1 < R1; ++k1) b[k1 * R2 + n2] = col[k1];
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < R1; ++k1) {
+      V row[R2];
+#pragma unroll
+      for (int n2 = 0; n2 < R2; ++n2) row[n2] = b[k1 * R2 + n2];
+      Dft<R2, S>::run(row);
+#pragma unroll
+      for (int k2 = 0; k2 < R2; ++k2) a[(E1 * k1 + E2 * k2) % R] = row[k2];
+    }
+  }
+};
+
+template <int S> struct Dft<6, S> : DftPFA<2, 3, S> {};
 template <int S> struct Dft<8, S> : DftComposite<2, 4, S> {};
 template <int S> struct Dft<9, S> : DftComposite<3, 3, S> {};
-template <int S> struct Dft<10, S> : DftComposite<2, 5, S> {};
-template <int S> struct Dft<12, S> : DftComposite<4, 3, S> {};
-template <int S> struct Dft<15, S> : DftComposite<3, 5, S> {};
+template <int S> struct Dft<10, S> : DftPFA<2, 5, S> {};
+template <int S> struct Dft<12, S> : DftPFA<4, 3, S> {};
+template <int S> struct Dft<15, S> : DftPFA<3, 5, S> {};
 template <int S> struct Dft<16, S> : DftComposite<4, 4, S> {};
-template <int S> struct Dft<20, S> : DftComposite<4, 5, S> {};
+template <int S> struct Dft<20, S> : DftPFA<4, 5, S> {};
 template <int S> struct Dft<25, S> : DftComposite<5, 5, S> {};
 template <int S> struct Dft<32, S> : DftComposite<4, 8, S> {};
 
