@@ -27,7 +27,30 @@ namespace qtam {
 
 namespace {
 
-// envelope storage conversions
+// envelope storage conversions; envelopes cross HBM exactly once, so they
+// are stored and loaded with the streaming (evict-first) cache policy and
+// leave the L2 to the spectra and accumulators
+template <typename S> __device__ __forceinline__ void stream_store(S* p, S v) {
+  if constexpr (sizeof(S) == 8) {
+    __stcs(reinterpret_cast<float2*>(p), *reinterpret_cast<float2*>(&v));
+  } else if constexpr (sizeof(S) == 16) {
+    __stcs(reinterpret_cast<double2*>(p), *reinterpret_cast<double2*>(&v));
+  } else {
+    __stcs(reinterpret_cast<unsigned int*>(p), *reinterpret_cast<unsigned int*>(&v));
+  }
+}
+template <typename S> __device__ __forceinline__ S stream_load(const S* p) {
+  S v;
+  if constexpr (sizeof(S) == 8) {
+    *reinterpret_cast<float2*>(&v) = __ldcs(reinterpret_cast<const float2*>(p));
+  } else if constexpr (sizeof(S) == 16) {
+    *reinterpret_cast<double2*>(&v) = __ldcs(reinterpret_cast<const double2*>(p));
+  } else {
+    *reinterpret_cast<unsigned int*>(&v) = __ldcs(reinterpret_cast<const unsigned int*>(p));
+  }
+  return v;
+}
+
 template <typename V, int E> struct Env;
 template <> struct Env<float2, ENV_F32> {
   using S = float2;
@@ -98,14 +121,14 @@ template <typename V, int E> struct StoreEnvelope {
   typename Env<V, E>::S* ys;
   bool valid;
   __device__ __forceinline__ void put(int, int i, V v) const {
-    if (valid) ys[i] = Env<V, E>::to(v);
+    if (valid) stream_store(&ys[i], Env<V, E>::to(v));
   }
 };
 template <typename V, int E> struct LoadEnvelope {
   const typename Env<V, E>::S* ys;
   bool valid;
   __device__ __forceinline__ V get(int, int i) const {
-    return valid ? Env<V, E>::from(ys[i]) : mk<V>(0, 0);
+    return valid ? Env<V, E>::from(stream_load(&ys[i])) : mk<V>(0, 0);
   }
 };
 
