@@ -6,6 +6,8 @@
 // selected at run time, so the kernels built on it stay in registers.
 #pragma once
 
+#include <type_traits>
+
 #include "fft_core.cuh"
 
 namespace qtam {
@@ -94,9 +96,21 @@ template <typename V, int NBS, int PS> struct SSmem {
   }
 };
 
-// Default strided accessors for the global-memory functors: element j + i*STEP.
+// Strided accessors for the global-memory functors: element j + i*STEP.  A
+// functor that defines its own get_s (e.g. to fold the stride into
+// addresses) is used as is.
+template <class F, class = void> struct HasGetS : std::false_type {};
+template <class F>
+struct HasGetS<F, std::void_t<decltype(&F::template get_s<1>)>> : std::true_type {};
+
 template <class F> struct Strided : F {
-  template <int STEP> __device__ __forceinline__ auto get_s(int b, int j, int i) const { return F::get(b, j + i * STEP); }
+  template <int STEP> __device__ __forceinline__ auto get_s(int b, int j, int i) const {
+    if constexpr (HasGetS<F>::value) {
+      return F::template get_s<STEP>(b, j, i);
+    } else {
+      return F::get(b, j + i * STEP);
+    }
+  }
   template <int STEP, typename V> __device__ __forceinline__ void put_s(int b, int j, int i, V v) const {
     F::put(b, j + i * STEP, v);
   }

@@ -116,6 +116,20 @@ template <typename T, bool FEXACT> struct LoadBand {
     if (in) x = Xs[r.kc + d];
     return cscale(x, w);
   }
+  // element e = j + s*STEP of a strided stage-0 read: the bin is k_c + e
+  // (low band) or k_c + e - M (high band); both addresses are a per-item base
+  // plus a compile-time offset
+  template <int STEP> __device__ __forceinline__ V get_s(int, int j, int s) const {
+    const int e = j + s * STEP;
+    const bool lo = e <= r.dhi;
+    const bool hi = e >= r.mlo;
+    const V* pl = Xs + (r.kc + j);
+    const V* ph = pl - r.M;
+    V x = mk<V>((T)0, (T)0);
+    if (lo) x = pl[s * STEP];
+    if (hi) x = ph[s * STEP];
+    return cscale(x, r.weight(hi ? e - r.M : e));
+  }
 };
 template <typename V, int E> struct StoreEnvelope {
   typename Env<V, E>::S* ys;
@@ -132,14 +146,23 @@ template <typename V, int E> struct LoadEnvelope {
   }
 };
 
-template <typename V> __device__ __forceinline__ void add_to(V* p, V v);
-template <> __device__ __forceinline__ void add_to<float2>(float2* p, float2 v) { atomicAdd(p, v); }
-template <> __device__ __forceinline__ void add_to<double2>(double2* p, double2 v) {
-  atomicAdd(&p->x, v.x);
-  atomicAdd(&p->y, v.y);
+// *p += v when `on` (relaxed, device scope); the float2 form is one
+// predicated vector reduction, so out-of-band positions cost no branch (the
+// accumulator is not read in the same kernel: no ordering with other accesses)
+__device__ __forceinline__ void add_if(float2* p, float2 v, bool on) {
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %3, 0; @q red.global.add.v2.f32 [%0], {%1, %2}; }"
+               :: "l"(p), "f"(v.x), "f"(v.y), "r"((int)on));
+}
+__device__ __forceinline__ void add_if(double2* p, double2 v, bool on) {
+  if (on) {
+    atomicAdd(&p->x, v.x);
+    atomicAdd(&p->y, v.y);
+  }
 }
 
-template <typename T, bool FEXACT> struct AccumulateBand {
+// PRED selects the predicated vector reduction; otherwise a branch around
+// the atomic (fewer live registers when the last stage holds 25 values)
+template <typename T, bool FEXACT, bool PRED> struct AccumulateBand {
   using V = cplx<T>;
   V* As;
   RowCtx<T, FEXACT> r;
@@ -148,7 +171,11 @@ template <typename T, bool FEXACT> struct AccumulateBand {
     int d;
     r.locate(i, in, d);
     const T w = r.weight(d);
-    if (in) add_to(&As[r.kc + d], cscale(v, w));
+    if constexpr (PRED) {
+      add_if(&As[r.kc + d], cscale(v, w), in);
+    } else if (in) {
+      add_if(&As[r.kc + d], cscale(v, w), true);
+    }
   }
 };
 
@@ -157,6 +184,7 @@ struct GenericEngine {
   RadixPlan rp;
   static constexpr int NBS = 0;
   static constexpr bool FEXACT = false;
+  static constexpr bool PRED_RED = false;
   __device__ __forceinline__ int m() const { return rp.m; }
   template <int S, typename V, class L, class St>
   __device__ __forceinline__ void run(V* sm, const V* tw, const L& ld, const St& st) const {
@@ -173,6 +201,7 @@ template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
   static constexpr int MINB = MINB_;
   static_assert(M_ <= 8192, "static variants need h < 4096 for the exact float window");
   static constexpr bool FEXACT = true;
+  static constexpr bool PRED_RED = radices[nrad - 1] < 25;
   __device__ __forceinline__ int m() const { return M; }
   template <int S, typename V, class L, class St>
   __device__ __forceinline__ void run(V* sm, const V* tws, const L& ld, const St& st) const {
@@ -237,7 +266,7 @@ __device__ __forceinline__ void rows_inverse_body(const Eng& eng, const RowDev<T
   const int64_t seg = valid ? unit / n_sel : 0;
   const int row = valid ? row_list[unit - seg * n_sel] : 0;
   LoadEnvelope<V, E> ld{y + (seg * n_rows + row) * M, valid};
-  AccumulateBand<T, Eng::FEXACT> stv{A + seg * Nr, row_ctx<T, Eng::FEXACT>(rows, row, M, Nr, valid, true)};
+  AccumulateBand<T, Eng::FEXACT, Eng::PRED_RED> stv{A + seg * Nr, row_ctx<T, Eng::FEXACT>(rows, row, M, Nr, valid, true)};
   eng.template run<-1>(sm, twM, ld, stv);
 }
 
