@@ -5,8 +5,9 @@ Segments are grouped by (sample rate, length); each group gets its own plan
 batched C entry points, which enqueue every group on one stream with one
 shared workspace.  ``UnevenBatch.capture()`` records the forward and inverse
 of all groups into a single CUDA graph, so a whole uneven batch is one graph
-launch; each group's kernels still cover the whole GPU (every group holds
-thousands of rows).  Row-kernel launch shapes come from the autotuner.
+launch; inside the graph the groups are spread over several forked streams
+(one workspace each), so independent groups run concurrently and fill each
+other's last waves.  Row-kernel launch shapes come from the autotuner.
 """
 from __future__ import annotations
 
@@ -81,6 +82,7 @@ class UnevenBatch:
         self.ws_bytes = max(qtam.qtam_batched_workspace_size(self.fwd), qtam.qtam_batched_workspace_size(self.inv))
         self.ws = torch.empty(self.ws_bytes, dtype=torch.uint8, device=dev)
         self.graph = None
+        self._stream_ws = {}
         self.envelope_bytes = sum(int(g.y.numel() * g.y.element_size()) for g in self.groups)
 
     # -- eager ---------------------------------------------------------------
@@ -95,18 +97,55 @@ class UnevenBatch:
         self.inverse(stream)
 
     # -- graph ---------------------------------------------------------------
-    def capture(self):
-        """Record forward + inverse of every group into one CUDA graph."""
+    def _lanes(self, n_streams):
+        """Split the groups over n_streams lanes (balanced by envelope bytes),
+        each lane with its own workspace."""
+        import torch
+        lanes = [[] for _ in range(n_streams)]
+        load = [0] * n_streams
+        for g in sorted(self.groups, key=lambda g: -int(g.y.numel())):
+            i = load.index(min(load))
+            lanes[i].append(g)
+            load[i] += int(g.y.numel())
+        out = []
+        for i, lane in enumerate(lanes):
+            if not lane:
+                continue
+            need = max(qtam.qtam_workspace_size(g.plan.handle, len(g.index)) for g in lane)
+            ws = self._stream_ws.get(i)
+            if ws is None or ws.numel() < need:
+                ws = torch.empty(need, dtype=torch.uint8, device=self.ws.device)
+                self._stream_ws[i] = ws
+            out.append((lane, ws))
+        return out
+
+    def capture(self, n_streams: int = 4):
+        """Record forward + inverse of every group into one CUDA graph.  The
+        groups are spread over n_streams forked streams (each with its own
+        workspace) so independent groups run concurrently and fill each
+        other's last waves; n_streams = 1 records them in order."""
         import torch
 
         self.roundtrip()                      # first call outside capture: tables and attributes exist
         torch.cuda.synchronize()
+        lanes = self._lanes(max(1, n_streams))
         g = torch.cuda.CUDAGraph()
         s = torch.cuda.Stream()
+        side = [torch.cuda.Stream() for _ in lanes]
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
             with torch.cuda.graph(g, stream=s):
-                self.roundtrip(torch.cuda.current_stream())
+                for lane_stream in side:
+                    lane_stream.wait_stream(s)            # fork
+                for (lane, ws), lane_stream in zip(lanes, side):
+                    with torch.cuda.stream(lane_stream):
+                        for grp in lane:
+                            b = len(grp.index)
+                            qtam.qtam_forward(grp.plan.handle, grp.x, b, grp.y, ws, ws.numel(), lane_stream)
+                            qtam.qtam_inverse(grp.plan.handle, grp.y, b, self.plane_mask, grp.xh, ws, ws.numel(),
+                                              lane_stream)
+                for lane_stream in side:
+                    s.wait_stream(lane_stream)            # join
         torch.cuda.current_stream().wait_stream(s)
         self.graph = g
         return g

@@ -70,9 +70,13 @@ def test_graph_replay_equals_eager(uneven):
     for g in ub.groups:
         g.y.zero_()
         g.xh.zero_()
-    ub.capture()
-    ub.replay()
-    torch.cuda.synchronize()
-    for g, ye, xe in zip(ub.groups, y_eager, x_eager):
-        assert torch.equal(torch.view_as_real(g.y), torch.view_as_real(ye))
-        assert float((g.xh - xe).norm() / xe.norm()) < 1e-6
+    for n_streams in (1, 3):
+        for g in ub.groups:
+            g.y.zero_()
+            g.xh.zero_()
+        ub.capture(n_streams=n_streams)
+        ub.replay()
+        torch.cuda.synchronize()
+        for g, ye, xe in zip(ub.groups, y_eager, x_eager):
+            assert torch.equal(torch.view_as_real(g.y), torch.view_as_real(ye))
+            assert float((g.xh - xe).norm() / xe.norm()) < 1e-6
