@@ -191,6 +191,15 @@ QTAM_API qtam_status qtam_roundtrip_host(qtam_plan_t plan, const void* x_host, i
                                 void* xhat_host, void* x_dev, void* y_dev, void* xhat_dev,
                                 void* workspace, size_t workspace_bytes, void* stream);
 
+/* Signal-quality metrics per Q-plane for optimal-plane selection (App. A,
+ * multi-Q bank, "optimal selection" mode): for every segment b and plane p,
+ * energy[b*P + p] = sum over rows and columns of |Y|^2 (accumulated in FP64)
+ * and peak[b*P + p] = max |Y|^2.  The plane with the largest energy (or peak)
+ * of each segment is its optimal plane.  energy (double) and peak (float) are
+ * device arrays of batch*P entries. */
+QTAM_API qtam_status qtam_plane_metrics(qtam_plan_t plan, const void* y, int64_t batch, double* energy, float* peak,
+                                        void* stream);
+
 /* Multiply every envelope row by a gain: y[b][p][k][*] *= gain[(b*P + p)*K + k]
  * (gain: device float array of batch*P*K entries).  Gain 0 zeroes a row --
  * the masked (row-zeroed) envelopes the inverse accepts; gain 1 leaves the

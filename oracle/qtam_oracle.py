@@ -313,3 +313,16 @@ def kappa(g: Geometry, planes=None, tau: float = 0.0) -> float:
             Wmax = np.maximum(Wmax, window(g, p, k))
     keep = kept_bins(Pf, tau)
     return float(np.max(Wmax[keep] / Pf[keep]))
+
+
+# ----------------------------------------------------------------------------
+# optimal-plane selection (App. A, multi-Q bank: "optimal selection" mode)
+# ----------------------------------------------------------------------------
+def plane_metrics(Y: np.ndarray):
+    """Per Q-plane signal-quality metrics of one segment's envelopes Y[P, K, M]:
+    total energy sum_{k,n} |Y|^2 and peak pixel intensity max_{k,n} |Y|^2, and
+    the plane each criterion selects (App. A: full scan vs optimal selection,
+    chosen independently for every signal)."""
+    e = np.sum(np.abs(Y) ** 2, axis=(1, 2))
+    pk = np.max(np.abs(Y) ** 2, axis=(1, 2))
+    return e, pk, int(np.argmax(e)), int(np.argmax(pk))

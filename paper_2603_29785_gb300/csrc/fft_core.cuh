@@ -235,6 +235,11 @@ template <int S> struct Dft<16, S> : DftComposite<4, 4, S> {};
 template <int S> struct Dft<20, S> : DftPFA<4, 5, S> {};
 template <int S> struct Dft<25, S> : DftComposite<5, 5, S> {};
 template <int S> struct Dft<32, S> : DftComposite<4, 8, S> {};
+template <int S> struct Dft<48, S> : DftPFA<16, 3, S> {};
+template <int S> struct Dft<64, S> : DftComposite<8, 8, S> {};
+template <int S> struct Dft<60, S> : DftPFA<4, 15, S> {};
+template <int S> struct Dft<75, S> : DftPFA<3, 25, S> {};
+template <int S> struct Dft<80, S> : DftPFA<16, 5, S> {};
 
 // items held in registers per thread for one stage of radix R (~16 complex)
 __host__ __device__ constexpr int ipt_for(int R) {

@@ -386,7 +386,59 @@ __global__ void k_scale_rows(typename Env<V, E>::S* __restrict__ y, const float*
   }
 }
 
+// Energy sum |Y|^2 and peak max |Y|^2 of one (segment, plane): a block per
+// pair, per-thread partial sums in FP64 (K*M terms), tree reduction.
+template <typename V, int E>
+__global__ void __launch_bounds__(256) k_plane_metrics(const typename Env<V, E>::S* __restrict__ y, int64_t per_plane,
+                                                       double* __restrict__ energy, float* __restrict__ peak) {
+  const int64_t pair = blockIdx.x;   // segment * P + plane
+  const typename Env<V, E>::S* p = y + pair * per_plane;
+  double e = 0.0;
+  float mx = 0.0f;
+  for (int64_t i = threadIdx.x; i < per_plane; i += blockDim.x) {
+    const V v = Env<V, E>::from(stream_load(&p[i]));
+    const double a2 = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+    e += a2;
+    mx = fmaxf(mx, (float)a2);
+  }
+  __shared__ double se[256];
+  __shared__ float sm[256];
+  se[threadIdx.x] = e;
+  sm[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      se[threadIdx.x] += se[threadIdx.x + s];
+      sm[threadIdx.x] = fmaxf(sm[threadIdx.x], sm[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    energy[pair] = se[0];
+    peak[pair] = sm[0];
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_plane_metrics(const void* y, int env, int64_t pairs, int64_t per_plane, double* energy, float* peak,
+                                 cudaStream_t st) {
+  if (pairs == 0) return cudaSuccess;
+  switch (env) {
+    case ENV_F64:
+      k_plane_metrics<double2, ENV_F64><<<(unsigned)pairs, 256, 0, st>>>(static_cast<const double2*>(y), per_plane, energy, peak);
+      break;
+    case ENV_BF16:
+      k_plane_metrics<float2, ENV_BF16><<<(unsigned)pairs, 256, 0, st>>>(static_cast<const __nv_bfloat162*>(y), per_plane, energy, peak);
+      break;
+    case ENV_F16:
+      k_plane_metrics<float2, ENV_F16><<<(unsigned)pairs, 256, 0, st>>>(static_cast<const __half2*>(y), per_plane, energy, peak);
+      break;
+    default:
+      k_plane_metrics<float2, ENV_F32><<<(unsigned)pairs, 256, 0, st>>>(static_cast<const float2*>(y), per_plane, energy, peak);
+  }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_scale_rows(void* y, int env, const float* gain, int64_t n_rows, int M, cudaStream_t st) {
   if (n_rows == 0) return cudaSuccess;

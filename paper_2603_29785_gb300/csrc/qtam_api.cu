@@ -866,6 +866,18 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
   return QTAM_OK;
 }
 
+qtam_status qtam_plane_metrics(qtam_plan_t pl, const void* y, int64_t B, double* energy, float* peak, void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK || B == 0) return s;
+  if (!y || !energy || !peak) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (!aligned(y, pl->env_size()) || !aligned(energy, 8) || !aligned(peak, 4)) return fail(QTAM_ERR_INVALID_ARG, "misaligned buffer");
+  if (B * pl->P > 0x7fffffff) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "too many (segment, plane) pairs");
+  DeviceGuard g(pl->device);
+  cudaError_t e = launch_plane_metrics(y, pl->env, B * pl->P, (int64_t)pl->K * pl->M, energy, peak,
+                                       static_cast<cudaStream_t>(stream));
+  return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "plane_metrics launch");
+}
+
 qtam_status qtam_scale_rows(qtam_plan_t pl, void* y, int64_t B, const float* gain, void* stream) {
   qtam_status s = common_checks(pl, B);
   if (s != QTAM_OK || B == 0) return s;

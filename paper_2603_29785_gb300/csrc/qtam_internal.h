@@ -74,6 +74,9 @@ struct RowVariant {
   RowInvFn inv[4];
 };
 int row_variant_count();
+// per (segment, plane) pair: energy = sum |Y|^2 (FP64), peak = max |Y|^2 over K*M values
+cudaError_t launch_plane_metrics(const void* y, int env, int64_t pairs, int64_t per_plane, double* energy, float* peak,
+                                 cudaStream_t st);
 // y[r][*] *= gain[r] for r < n_rows (device gains), envelope storage kind env
 cudaError_t launch_scale_rows(void* y, int env, const float* gain, int64_t n_rows, int M, cudaStream_t st);
 const RowVariant* row_variant(int i);   // nullptr when out of range

@@ -89,6 +89,7 @@ SIGNATURES = {
     "qtam_roundtrip_host": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P, _P, _P, _P, _SZ, _P]),
     "qtam_forward_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
     "qtam_scale_rows": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "qtam_plane_metrics": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
     "qtam_batched_workspace_size": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_SZ)]),
     "qtam_forward_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _SZ, _P]),
     "qtam_inverse_batched": (ctypes.c_int, [_P, ctypes.c_int32, _U64, _P, _SZ, _P]),
@@ -258,6 +259,10 @@ def qtam_forward_noalloc(plan, x, batch, y, stream=None):
     """qtam_forward with the library's fixed scratch array instead of a
     caller workspace (for callers that cannot allocate at call time)."""
     _check(lib().qtam_forward_noalloc(plan, _ptr(x), int(batch), _ptr(y), _stream(stream)))
+
+
+def qtam_plane_metrics(plan, y, batch, energy, peak, stream=None):
+    _check(lib().qtam_plane_metrics(plan, _ptr(y), int(batch), _ptr(energy), _ptr(peak), _stream(stream)))
 
 
 def qtam_scale_rows(plan, y, batch, gain, stream=None):
@@ -431,6 +436,17 @@ class Plan:
         ws, wsb = self.workspace(B)
         qtam_inverse(self.handle, y, B, plane_mask, x, ws, wsb, stream)
         return x
+
+    def plane_metrics(self, y, stream=None):
+        """(energy [B, P] float64, peak [B, P] float32, best plane by energy [B],
+        best plane by peak [B]) -- optimal-plane selection per segment."""
+        import torch
+        self._check_y(y)
+        B = y.shape[0]
+        energy = torch.empty((B, self.P), dtype=torch.float64, device=y.device)
+        peak = torch.empty((B, self.P), dtype=torch.float32, device=y.device)
+        qtam_plane_metrics(self.handle, y, B, energy, peak, stream)
+        return energy, peak, energy.argmax(dim=1), peak.argmax(dim=1)
 
     def scale_rows(self, y, gain, stream=None):
         """y[b, p, k, :] *= gain[b, p, k] in place (gain: CUDA float32 [batch, P, K])."""

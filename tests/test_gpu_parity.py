@@ -278,3 +278,67 @@ def test_device_errors_are_reported():
     with pytest.raises(qtam.QtamError) as e:
         qtam.qtam_forward(p.handle, x, 4, y, ws, 16)
     assert e.value.status == 9
+
+
+def test_plane_metrics_and_optimal_plane():
+    """Optimal-plane selection: per-plane energy and peak of the envelopes match the
+    oracle and select the same plane for every segment."""
+    p = make(4096.0, 32768, (4.0, 8.0, 16.0, 32.0, 64.0), 20.0, 2048.0, 64)
+    g = geom_of(p)
+    B = 4
+    x = np.stack([synth.glitchy_segment(40 + b, g.N, 4096.0, chirp=True) for b in range(B)])
+    y = p.forward(dev(x))
+    energy, peak, best_e, best_p = p.plane_metrics(y)
+    torch.cuda.synchronize()
+    Yg = env_np(p, y)
+    for b in range(B):
+        e, pk, be, bp = O.plane_metrics(O.forward(g, x[b].astype(np.float64)))
+        assert np.allclose(energy[b].cpu().numpy(), e, rtol=2e-6)
+        assert np.allclose(peak[b].cpu().numpy(), pk, rtol=5e-6)
+        e_gpu, pk_gpu, _, _ = O.plane_metrics(Yg[b])          # same reduction of the GPU envelopes
+        assert np.allclose(energy[b].cpu().numpy(), e_gpu, rtol=1e-9)
+        assert int(best_e[b]) == int(np.argmax(e_gpu)) and int(best_p[b]) == int(np.argmax(pk_gpu))
+
+
+def test_edge_M_equals_largest_window():
+    """M = L_max exactly (45): every baseband position holds a band offset."""
+    p = make(64.0, 512, (4.0, 8.0), 3.0, 29.0, 12)
+    g = geom_of(p)
+    assert p.M == int(g.L.max()) == 45
+    x = synth.white(61, g.N).astype(np.float32)
+    y = p.forward(dev(x[None]))
+    Y = env_np(p, y)[0]
+    ref = O.forward(g, x.astype(np.float64))
+    assert rel(Y, ref) < FWD_FROB["f32"]
+    xh = host(p.inverse(y))[0]
+    assert rel(xh, O.projection(g, x.astype(np.float64), tau=p.info["p_floor_rel"])) < RT["f32"]
+
+
+def test_edge_single_row_unclamped():
+    """K = 1: no neighbouring centre, so no clamp; one window of half-width 44."""
+    p = make(64.0, 512, (6.0,), 10.0, 10.0, 1)
+    g = geom_of(p)
+    assert g.K == 1 and int(g.h[0, 0]) == 44
+    x = synth.white(62, g.N).astype(np.float32)
+    y = p.forward(dev(x[None]))
+    assert rel(env_np(p, y)[0], O.forward(g, x.astype(np.float64))) < FWD_FROB["f32"]
+    xh = host(p.inverse(y))[0]
+    assert rel(xh, O.projection(g, x.astype(np.float64), tau=p.info["p_floor_rel"])) < RT["f32"]
+
+
+def test_edge_batch_above_grid_y_limit():
+    """65540 segments: the long-FFT launches split the batch at 65535 grid rows."""
+    p = make(256.0, 256, (2.0,), 20.0, 60.0, 2)
+    g = geom_of(p)
+    B = 65540
+    rng = synth.rng(63)
+    x = rng.standard_normal((B, g.N)).astype(np.float32)
+    xd = dev(x)
+    y = p.forward(xd)
+    xh = p.inverse(y)
+    torch.cuda.synchronize()
+    tau = p.info["p_floor_rel"]
+    for b in (0, 65534, 65535, 65536, B - 1):
+        xb = x[b].astype(np.float64)
+        assert rel(y[b].cpu().numpy().astype(np.complex128), O.forward(g, xb)) < FWD_FROB["f32"], b
+        assert rel(xh[b].cpu().numpy().astype(np.float64), O.projection(g, xb, tau=tau)) < RT["f32"], b

@@ -350,3 +350,30 @@ def test_windows_truncated_at_band_edges():
         d, fb = O.band(g, 0, k)
         assert fb.min() >= 0 and fb.max() <= g.N // 2
         assert d.size < g.L[0, k]
+
+
+# --------------------------------------------------------------------------- optimal-plane selection
+def test_plane_energy_is_per_plane_frame_identity():
+    """Energy of plane p = (1/N) sum_f P_p[f] |X[f]|^2 (App. C frame operator of
+    that plane alone), which the metric must reproduce."""
+    g = small_geom()
+    x = _rand_x(g.N, 21)
+    X = np.fft.rfft(x)
+    e, pk, best_e, best_p = O.plane_metrics(O.forward(g, x))
+    for p in range(g.P):
+        ref = np.sum(O.frame_operator(g, planes=[p]) * np.abs(X) ** 2) / g.N
+        assert e[p] == pytest.approx(ref, rel=1e-12)
+    assert best_e == int(np.argmax(e)) and best_p == int(np.argmax(pk))
+
+
+def test_plane_peak_of_a_tone_closed_form():
+    """A cosine on row k's centre bin gives |Y_k[n]|^2 = W_k[b]^2 N / (4 M) on every
+    column (one spectral line, shifted to DC): the peak of each plane is that value
+    on its strongest row."""
+    g = O.geometry(64.0, 512, (4.0, 8.0), 3.0, 30.0, 12, norm="none")
+    b = int(g.kc[0, 5])
+    x = np.cos(2 * np.pi * b * np.arange(g.N) / g.N)
+    e, pk, _, _ = O.plane_metrics(O.forward(g, x))
+    for p in range(g.P):
+        wmax = max(O.window(g, p, k)[b] for k in range(g.K))
+        assert pk[p] == pytest.approx(wmax ** 2 * g.N / (4 * g.M), rel=1e-12)
