@@ -99,6 +99,8 @@ class Geometry:
     kc: np.ndarray          # [P, K] centre bins
     h: np.ndarray           # [P, K] half-widths
     c: np.ndarray           # [P, K] window normalisation c_k
+    window: str = "bisquare"
+    window_param: float = 0.0
     extra: dict = field(default_factory=dict)
 
     @property
@@ -132,10 +134,58 @@ def bisquare_profile(d: np.ndarray, h: int) -> np.ndarray:
     return np.where(a <= h, u * u, 0.0)
 
 
-def window_norm(h: int, norm: str) -> float:
+WINDOWS = ("bisquare", "hann", "kaiser", "tukey", "planck")
+
+
+def window_profile(d: np.ndarray, h: int, window: str = "bisquare", param: float = 0.0) -> np.ndarray:
+    """Unnormalised spectral window W'(d), |d| <= h, of App. A with u = d/h:
+
+    bisquare  (1 - u^2)^2                              (Eq. gwpy_window_formula)
+    hann      (1 + cos(pi u)) / 2
+    kaiser    I0(beta sqrt(1 - u^2)) / I0(beta),        param = beta
+    tukey     1 on |u| <= 1 - a; (1 + cos(pi (|u| - (1 - a)) / a)) / 2 beyond,  param = a
+    planck    1 on |u| <= 1 - a; 1 / (exp(Z) + 1) beyond with t = 1 - |u|,
+              Z = a / t - a / (a - t),  param = a
+    The printed Planck exponent adds both terms; taken literally the window would
+    jump from 1 to 0 at the plateau edge, so the standard continuous form (the
+    second term with the opposite sign) is used.
+    """
+    if window == "bisquare":
+        return bisquare_profile(d, h)
+    d = np.asarray(d, dtype=np.int64)
+    a = np.abs(d)
+    u = a.astype(np.float64) / float(h)
+    w = np.zeros(u.shape)
+    inside = a <= h
+    if window == "hann":
+        w = 0.5 * (1.0 + np.cos(np.pi * u))
+    elif window == "kaiser":
+        beta = float(param)
+        w = np.i0(beta * np.sqrt(np.clip(1.0 - u * u, 0.0, None))) / np.i0(beta)
+    elif window == "tukey":
+        al = float(param)
+        w = np.ones(u.shape)
+        if al > 0:
+            edge = u > 1.0 - al
+            w[edge] = 0.5 * (1.0 + np.cos(np.pi * (u[edge] - (1.0 - al)) / al))
+    elif window == "planck":
+        al = float(param)
+        w = np.ones(u.shape)
+        t = 1.0 - u
+        edge = (t < al) & (t > 0)
+        if al > 0:
+            z = al / t[edge] - al / (al - t[edge])
+            w[edge] = 1.0 / (np.exp(np.clip(z, -700, 700)) + 1.0)
+        w[t <= 0] = 0.0
+    else:
+        raise ValueError(window)
+    return np.where(inside, w, 0.0)
+
+
+def window_norm(h: int, norm: str, window: str = "bisquare", param: float = 0.0) -> float:
     """c_k of Eq. gwpy_window_and_normalization under reading C4."""
     d = np.arange(-h, h + 1)
-    s2 = float(np.sum(bisquare_profile(d, h) ** 2))
+    s2 = float(np.sum(window_profile(d, h, window, param) ** 2))
     if norm == "l2":
         return 1.0 / math.sqrt(s2)
     if norm == "paper":
@@ -146,7 +196,7 @@ def window_norm(h: int, norm: str) -> float:
 
 
 def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
-             max_window_hz=0.0, n_out=0) -> Geometry:
+             max_window_hz=0.0, n_out=0, window="bisquare", window_param=0.0) -> Geometry:
     """Plan the filter bank: grid, centre bins, half-widths, c_k and M.
 
     App. A (grid f_k, L_k^ideal proportional to f_k N_t / Q, automatic clamp
@@ -179,7 +229,7 @@ def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
             kc[p, k] = round_half_away(grid[k] * T)
             h_ideal = int(math.floor(grid[k] * T * q_width / Q))
             h[p, k] = max(1, min(h_ideal, h_max))
-            c[p, k] = window_norm(int(h[p, k]), norm)
+            c[p, k] = window_norm(int(h[p, k]), norm, window, window_param)
     Lmax = int(np.max(2 * h + 1))
     if n_out:
         if n_out < Lmax:
@@ -189,13 +239,14 @@ def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
         M = smooth_length(Lmax)
     return Geometry(fs=float(fs), N=N, qs=tuple(float(q) for q in qs), fmin=float(fmin),
                     fmax=float(fmax), K=int(K), norm=norm, q_width=float(q_width),
-                    h_max=int(h_max), M=M, f=f, kc=kc, h=h, c=c)
+                    h_max=int(h_max), M=M, f=f, kc=kc, h=h, c=c, window=window,
+                    window_param=float(window_param))
 
 
 def window(g: Geometry, p: int, k: int) -> np.ndarray:
     """Dense W_k[f], f = 0..N/2, truncated to the one-sided band (reading C6)."""
     fbin = np.arange(g.Nr)
-    return g.c[p, k] * bisquare_profile(fbin - g.kc[p, k], int(g.h[p, k]))
+    return g.c[p, k] * window_profile(fbin - g.kc[p, k], int(g.h[p, k]), g.window, g.window_param)
 
 
 def frame_operator(g: Geometry, planes=None) -> np.ndarray:
@@ -241,7 +292,7 @@ def forward_row(g: Geometry, X: np.ndarray, p: int, k: int) -> np.ndarray:
     """
     d, fb = band(g, p, k)
     Z = np.zeros(g.M, dtype=np.complex128)
-    w = g.c[p, k] * bisquare_profile(d, int(g.h[p, k]))
+    w = g.c[p, k] * window_profile(d, int(g.h[p, k]), g.window, g.window_param)
     Z[d % g.M] = w * X[fb]
     return np.fft.ifft(Z) * math.sqrt(g.M / g.N)
 
@@ -269,7 +320,7 @@ def accumulate(g: Geometry, Y: np.ndarray, planes=None) -> np.ndarray:
         for k in range(g.K):
             S = np.fft.fft(Y[p, k]) * math.sqrt(g.N / g.M)
             d, fb = band(g, p, k)
-            w = g.c[p, k] * bisquare_profile(d, int(g.h[p, k]))
+            w = g.c[p, k] * window_profile(d, int(g.h[p, k]), g.window, g.window_param)
             A[fb] += w * S[d % g.M]
     return A
 

@@ -53,8 +53,8 @@ def _profile_linear(d, h):
     return np.sqrt(_orig_profile(d, h))
 
 
-def _norm_sum_not_sqrt(h, norm):
-    c = _orig_norm(h, norm)
+def _norm_sum_not_sqrt(h, norm, *args):
+    c = _orig_norm(h, norm, *args)
     return c * c if norm == "l2" else c
 
 

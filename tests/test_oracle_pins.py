@@ -377,3 +377,47 @@ def test_plane_peak_of_a_tone_closed_form():
     for p in range(g.P):
         wmax = max(O.window(g, p, k)[b] for k in range(g.K))
         assert pk[p] == pytest.approx(wmax ** 2 * g.N / (4 * g.M), rel=1e-12)
+
+
+# --------------------------------------------------------------------------- window family (App. A)
+def test_window_family_special_cases_and_moments():
+    """Closed forms: Tukey a=1 is Hann, Tukey a=0 and Kaiser beta=0 are the
+    rectangle, sum of Hann^2 -> 3h/4 (int_{-1}^{1} cos^4(pi u/2) du = 3/4),
+    Planck-taper is continuous (plateau 1, -> 0 at the edge, monotone in between)."""
+    h = 4000
+    d = np.arange(-h, h + 1)
+    hann = O.window_profile(d, h, "hann")
+    assert np.allclose(O.window_profile(d, h, "tukey", 1.0), hann, atol=1e-15)
+    assert np.all(O.window_profile(d, h, "tukey", 0.0) == 1.0)
+    assert np.allclose(O.window_profile(d, h, "kaiser", 0.0), 1.0, atol=1e-15)
+    assert np.sum(hann ** 2) / h == pytest.approx(0.75, rel=1e-3)
+    assert hann[h] == 1.0 and hann[0] == pytest.approx(0.0, abs=1e-15)
+    k = O.window_profile(d, h, "kaiser", 8.0)
+    assert k[h] == pytest.approx(1.0) and k[0] == pytest.approx(1.0 / np.i0(8.0))
+    pl = O.window_profile(d, h, "planck", 0.25)
+    half = pl[h:]                      # d = 0 .. h
+    assert np.all(half[: int(0.75 * h)] == 1.0) and half[-1] == 0.0
+    assert np.all(np.diff(half) <= 1e-15)                     # non-increasing away from the centre
+    assert np.max(np.abs(np.diff(half))) < 0.01               # continuous: no jump at the plateau edge
+    # the taper is symmetric about its midpoint: w(t) + w(a - t) = 1, t = 1 - |u|
+    t = 0.1
+    u1, u2 = 1 - t, 1 - (0.25 - t)
+    w1 = O.window_profile(np.array([int(round(u1 * h))]), h, "planck", 0.25)[0]
+    w2 = O.window_profile(np.array([int(round(u2 * h))]), h, "planck", 0.25)[0]
+    assert w1 + w2 == pytest.approx(1.0, abs=2e-3)
+
+
+@pytest.mark.parametrize("window,param", [("hann", 0.0), ("kaiser", 6.0), ("tukey", 0.5), ("planck", 0.3)])
+def test_window_family_frame_identities(window, param):
+    """App. C holds for any window: round trip = projection, frame energy identity."""
+    g = small_geom(window=window, window_param=param)
+    x = _rand_x(g.N, 31)
+    Y = O.forward(g, x)
+    assert np.linalg.norm(O.inverse(g, Y) - O.projection(g, x)) < 1e-12 * np.linalg.norm(x)
+    X = np.fft.rfft(x)
+    assert np.sum(np.abs(Y) ** 2) == pytest.approx(np.sum(O.frame_operator(g) * np.abs(X) ** 2) / g.N, rel=1e-12)
+    for p in range(g.P):
+        for k in range(g.K):
+            hk = int(g.h[p, k])
+            w = g.c[p, k] * O.window_profile(np.arange(-hk, hk + 1), hk, window, param)
+            assert np.sum(w ** 2) == pytest.approx(1.0, rel=1e-12)
