@@ -71,7 +71,11 @@ typedef enum {
   QTAM_ERR_WORKSPACE = 9         /* workspace smaller than qtam_workspace_size() */
 } qtam_status;
 
-enum { QTAM_WIN_BISQUARE = 0 };
+/* spectral windows of App. A on |d| <= h, u = d/h: bisquare (1-u^2)^2;
+ * Hann (1+cos(pi u))/2; Kaiser I0(beta sqrt(1-u^2))/I0(beta) (window_param =
+ * beta); Tukey with taper fraction a (window_param = a); Planck-taper with
+ * taper fraction a (window_param = a, standard continuous form). */
+enum { QTAM_WIN_BISQUARE = 0, QTAM_WIN_HANN = 1, QTAM_WIN_KAISER = 2, QTAM_WIN_TUKEY = 3, QTAM_WIN_PLANCK = 4 };
 /* window normalisation c_k: L2 = (sum W'^2)^(-1/2) (unit-energy window);
  * PAPER = 1 / sum W'^2 (Eq. gwpy_window_and_normalization read literally);
  * NONE = 1. */
@@ -85,7 +89,7 @@ typedef struct {
   int32_t n_q;            /* 1 .. 64 */
   double f_min, f_max;    /* log grid f_k = f_min (f_max/f_min)^(k/(K-1)), endpoints included */
   int32_t rows_per_plane; /* K >= 1 */
-  int32_t window;         /* QTAM_WIN_BISQUARE */
+  int32_t window;         /* QTAM_WIN_*; non-bisquare windows run the runtime-engine kernels */
   int32_t norm;           /* QTAM_NORM_* */
   double q_width;         /* half-width h = floor(f T q_width / Q); <= 0 selects sqrt(11) */
   double max_window_hz;   /* 0: automatic clamp from the largest centre gap (App. A); > 0: manual */
@@ -93,6 +97,8 @@ typedef struct {
   int32_t compute_dtype;  /* QTAM_DTYPE_F32 or QTAM_DTYPE_F64 */
   int32_t envelope_dtype; /* F32/BF16/F16 with F32 compute; F64 with F64 compute */
   double p_floor_rel;     /* tau; < 0 selects the default (1e-6 for F32, 0 for F64) */
+  double window_param;    /* Kaiser beta in [0, 100]; Tukey / Planck taper fraction in [0, 1];
+                             ignored for bisquare and Hann; anything else -> QTAM_ERR_INVALID_ARG */
 } qtam_plan_desc;
 
 typedef struct {

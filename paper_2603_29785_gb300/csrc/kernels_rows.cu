@@ -81,10 +81,15 @@ template <> struct Env<double2, ENV_F64> {
 // 0..N/2; baseband position i holds d = i for i <= dhi and d = i - M for
 // i >= M + dlo.  The weight is c W'(d) = (kw (h^2 - d^2))^2 with
 // kw = sqrt(c)/h^2; with FEXACT (h < 4096) h^2 - d^2 is formed exactly in
-// floating point, otherwise as the integer product (h - |d|)(h + |d|).
+// floating point, otherwise as the integer product (h - |d|)(h + |d|).  The
+// other App. A windows (runtime engine only) read W'(|d|) from a per-plan
+// table instead; positions outside the band read W'(h) and are multiplied
+// by a zero bin.
 template <typename T, bool FEXACT> struct RowCtx {
   int kc, h, M, dhi, mlo;
   T kw, h2;
+  const T* wt;   // runtime engine only: W'(0..h) table of a non-bisquare window, or null
+  T cw;          // its normalisation (c_fwd or c_inv)
   __device__ __forceinline__ void locate(int i, bool& in, int& d) const {
     const bool lo = i <= dhi;
     in = lo || i >= mlo;
@@ -97,6 +102,7 @@ template <typename T, bool FEXACT> struct RowCtx {
       u = (h2 - df * df) * kw;
     } else {
       const int a = d < 0 ? -d : d;
+      if (wt) return cw * wt[a <= h ? a : h];
       u = (T)(h - a) * (T)(h + a) * kw;
     }
     return u * u;
@@ -212,9 +218,11 @@ template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
 
 template <typename T, bool FEXACT>
 __device__ __forceinline__ RowCtx<T, FEXACT> row_ctx(const RowDev<T>* rows, int row, int M, int64_t Nr, bool valid,
-                                                     bool inv) {
+                                                     bool inv, const T* wtab) {
   RowCtx<T, FEXACT> r;
   r.M = M;
+  r.wt = nullptr;
+  r.cw = (T)0;
   if (valid) {
     const RowDev<T> rd = rows[row];
     const int nhalf = (int)(Nr - 1);
@@ -222,6 +230,10 @@ __device__ __forceinline__ RowCtx<T, FEXACT> row_ctx(const RowDev<T>* rows, int 
     r.h = rd.h;
     r.kw = inv ? rd.kw_inv : rd.kw_fwd;
     r.h2 = (T)rd.h * (T)rd.h;
+    if (wtab && rd.woff >= 0) {
+      r.wt = wtab + rd.woff;
+      r.cw = inv ? rd.c_inv : rd.c_fwd;
+    }
     r.dhi = min(rd.h, nhalf - rd.kc);     // may be < 0: no non-negative offset
     r.mlo = M + max(-rd.h, -rd.kc);       // may be > M - 1: no negative offset
     if (r.dhi < -1) r.dhi = -1;
@@ -237,7 +249,7 @@ template <class Eng, typename T, int E>
 __device__ __forceinline__ void rows_forward_body(const Eng& eng, const RowDev<T>* __restrict__ rows, int n_rows,
                                                   int64_t Nr, const cplx<T>* __restrict__ X,
                                                   typename Env<cplx<T>, E>::S* __restrict__ y, int64_t n_units,
-                                                  const cplx<T>* __restrict__ twM) {
+                                                  const cplx<T>* __restrict__ twM, const T* __restrict__ wtab) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -246,7 +258,7 @@ __device__ __forceinline__ void rows_forward_body(const Eng& eng, const RowDev<T
   const bool valid = unit < n_units;
   const int64_t seg = valid ? unit / n_rows : 0;
   const int row = valid ? (int)(unit - seg * n_rows) : 0;
-  LoadBand<T, Eng::FEXACT> ld{X + seg * Nr, row_ctx<T, Eng::FEXACT>(rows, row, M, Nr, valid, false)};
+  LoadBand<T, Eng::FEXACT> ld{X + seg * Nr, row_ctx<T, Eng::FEXACT>(rows, row, M, Nr, valid, false, wtab)};
   StoreEnvelope<V, E> stv{y + (valid ? unit : 0) * M, valid};
   eng.template run<+1>(sm, twM, ld, stv);
 }
@@ -256,7 +268,7 @@ __device__ __forceinline__ void rows_inverse_body(const Eng& eng, const RowDev<T
                                                   const int* __restrict__ row_list, int n_sel, int n_rows, int64_t Nr,
                                                   const typename Env<cplx<T>, E>::S* __restrict__ y,
                                                   cplx<T>* __restrict__ A, int64_t n_units,
-                                                  const cplx<T>* __restrict__ twM) {
+                                                  const cplx<T>* __restrict__ twM, const T* __restrict__ wtab) {
   using V = cplx<T>;
   extern __shared__ __align__(16) unsigned char smraw[];
   V* sm = reinterpret_cast<V*>(smraw);
@@ -266,7 +278,8 @@ __device__ __forceinline__ void rows_inverse_body(const Eng& eng, const RowDev<T
   const int64_t seg = valid ? unit / n_sel : 0;
   const int row = valid ? row_list[unit - seg * n_sel] : 0;
   LoadEnvelope<V, E> ld{y + (seg * n_rows + row) * M, valid};
-  AccumulateBand<T, Eng::FEXACT, Eng::PRED_RED> stv{A + seg * Nr, row_ctx<T, Eng::FEXACT>(rows, row, M, Nr, valid, true)};
+  AccumulateBand<T, Eng::FEXACT, Eng::PRED_RED> stv{A + seg * Nr,
+                                                    row_ctx<T, Eng::FEXACT>(rows, row, M, Nr, valid, true, wtab)};
   eng.template run<-1>(sm, twM, ld, stv);
 }
 
@@ -274,29 +287,29 @@ template <typename T, int E>
 __global__ void __launch_bounds__(kMaxBlock, 1)
     k_rows_forward(GenericEngine eng, const RowDev<T>* __restrict__ rows, int n_rows, int64_t Nr,
                    const cplx<T>* __restrict__ X, typename Env<cplx<T>, E>::S* __restrict__ y, int64_t n_units,
-                   const cplx<T>* __restrict__ twM) {
-  rows_forward_body<GenericEngine, T, E>(eng, rows, n_rows, Nr, X, y, n_units, twM);
+                   const cplx<T>* __restrict__ twM, const T* __restrict__ wtab) {
+  rows_forward_body<GenericEngine, T, E>(eng, rows, n_rows, Nr, X, y, n_units, twM, wtab);
 }
 template <typename T, int E>
 __global__ void __launch_bounds__(kMaxBlock, 1)
     k_rows_inverse(GenericEngine eng, const RowDev<T>* __restrict__ rows, const int* __restrict__ row_list, int n_sel,
                    int n_rows, int64_t Nr, const typename Env<cplx<T>, E>::S* __restrict__ y, cplx<T>* __restrict__ A,
-                   int64_t n_units, const cplx<T>* __restrict__ twM) {
-  rows_inverse_body<GenericEngine, T, E>(eng, rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM);
+                   int64_t n_units, const cplx<T>* __restrict__ twM, const T* __restrict__ wtab) {
+  rows_inverse_body<GenericEngine, T, E>(eng, rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM, wtab);
 }
 
 template <class Eng, int E>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
     k_rows_forward_s(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
                      typename Env<float2, E>::S* __restrict__ y, int64_t n_units, const float2* __restrict__ twM) {
-  rows_forward_body<Eng, float, E>(Eng(), rows, n_rows, Nr, X, y, n_units, twM);
+  rows_forward_body<Eng, float, E>(Eng(), rows, n_rows, Nr, X, y, n_units, twM, nullptr);
 }
 template <class Eng, int E>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
     k_rows_inverse_s(const RowDev<float>* __restrict__ rows, const int* __restrict__ row_list, int n_sel, int n_rows,
                      int64_t Nr, const typename Env<float2, E>::S* __restrict__ y, float2* __restrict__ A,
                      int64_t n_units, const float2* __restrict__ twM) {
-  rows_inverse_body<Eng, float, E>(Eng(), rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM);
+  rows_inverse_body<Eng, float, E>(Eng(), rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM, nullptr);
 }
 
 // ---- registry of compile-time variants (FP32 compute) ------------------------
@@ -459,7 +472,7 @@ const RowVariant* row_variant(int i) { return (i >= 0 && i < row_variant_count()
 
 template <typename T>
 cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_rows, int64_t Nr, const cplx<T>* X,
-                                void* y, int env, int64_t B, const cplx<T>* twM, cudaStream_t st) {
+                                void* y, int env, int64_t B, const cplx<T>* twM, cudaStream_t st, const T* wtab) {
   const int64_t units = B * n_rows;
   if (units == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
@@ -473,22 +486,22 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
       case ENV_BF16:
         allow_smem((const void*)k_rows_forward<T, ENV_BF16>, c.smem);
         k_rows_forward<T, ENV_BF16><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
-                                                                       static_cast<__nv_bfloat162*>(y), units, twM);
+                                                                       static_cast<__nv_bfloat162*>(y), units, twM, wtab);
         break;
       case ENV_F16:
         allow_smem((const void*)k_rows_forward<T, ENV_F16>, c.smem);
         k_rows_forward<T, ENV_F16><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
-                                                                      static_cast<__half2*>(y), units, twM);
+                                                                      static_cast<__half2*>(y), units, twM, wtab);
         break;
       default:
         allow_smem((const void*)k_rows_forward<T, ENV_F32>, c.smem);
         k_rows_forward<T, ENV_F32><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
-                                                                      static_cast<float2*>(y), units, twM);
+                                                                      static_cast<float2*>(y), units, twM, wtab);
     }
   } else {
     allow_smem((const void*)k_rows_forward<T, ENV_F64>, c.smem);
     k_rows_forward<T, ENV_F64><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
-                                                                  static_cast<double2*>(y), units, twM);
+                                                                  static_cast<double2*>(y), units, twM, wtab);
   }
   return cudaGetLastError();
 }
@@ -496,7 +509,7 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
 template <typename T>
 cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const int* row_list, int n_sel, int n_rows,
                                 int64_t Nr, const void* y, int env, cplx<T>* A, int64_t B, const cplx<T>* twM,
-                                cudaStream_t st) {
+                                cudaStream_t st, const T* wtab) {
   const int64_t units = B * n_sel;
   if (units == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
@@ -510,33 +523,35 @@ cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const in
       case ENV_BF16:
         allow_smem((const void*)k_rows_inverse<T, ENV_BF16>, c.smem);
         k_rows_inverse<T, ENV_BF16><<<blocks, c.threads, c.smem, st>>>(
-            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __nv_bfloat162*>(y), A, units, twM);
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __nv_bfloat162*>(y), A, units, twM, wtab);
         break;
       case ENV_F16:
         allow_smem((const void*)k_rows_inverse<T, ENV_F16>, c.smem);
         k_rows_inverse<T, ENV_F16><<<blocks, c.threads, c.smem, st>>>(
-            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __half2*>(y), A, units, twM);
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __half2*>(y), A, units, twM, wtab);
         break;
       default:
         allow_smem((const void*)k_rows_inverse<T, ENV_F32>, c.smem);
         k_rows_inverse<T, ENV_F32><<<blocks, c.threads, c.smem, st>>>(
-            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, twM);
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, twM, wtab);
     }
   } else {
     allow_smem((const void*)k_rows_inverse<T, ENV_F64>, c.smem);
     k_rows_inverse<T, ENV_F64><<<blocks, c.threads, c.smem, st>>>(
-        eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const double2*>(y), A, units, twM);
+        eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const double2*>(y), A, units, twM, wtab);
   }
   return cudaGetLastError();
 }
 
 template cudaError_t launch_rows_forward<float>(const RowCfg&, const RowDev<float>*, int, int64_t, const float2*, void*,
-                                                int, int64_t, const float2*, cudaStream_t);
+                                                int, int64_t, const float2*, cudaStream_t, const float*);
 template cudaError_t launch_rows_forward<double>(const RowCfg&, const RowDev<double>*, int, int64_t, const double2*,
-                                                 void*, int, int64_t, const double2*, cudaStream_t);
+                                                 void*, int, int64_t, const double2*, cudaStream_t, const double*);
 template cudaError_t launch_rows_inverse<float>(const RowCfg&, const RowDev<float>*, const int*, int, int, int64_t,
-                                                const void*, int, float2*, int64_t, const float2*, cudaStream_t);
+                                                const void*, int, float2*, int64_t, const float2*, cudaStream_t,
+                                                const float*);
 template cudaError_t launch_rows_inverse<double>(const RowCfg&, const RowDev<double>*, const int*, int, int, int64_t,
-                                                 const void*, int, double2*, int64_t, const double2*, cudaStream_t);
+                                                 const void*, int, double2*, int64_t, const double2*, cudaStream_t,
+                                                 const double*);
 
 }  // namespace qtam

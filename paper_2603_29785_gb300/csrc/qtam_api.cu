@@ -5,7 +5,8 @@
 // Q-plane, window length proportional to f_k N_t / Q clamped at
 // L_max = 2 floor(ceil(N_t Delta f_max) / 2) + 1 (Delta f_max = largest gap
 // between neighbouring centres, or a manual clamp), centre bin k_c = f_k N_t
-// (Eq. support), bisquare windows (Eq. gwpy_window_formula) and an envelope
+// (Eq. support), bisquare windows (Eq. gwpy_window_formula; Hann, Kaiser,
+// Tukey and Planck-taper as the App. A alternatives) and an envelope
 // length M no shorter than the largest window (Sec. III, lossless
 // decimation).  Where the paper leaves a constant open the choices are:
 // h = max(1, min(floor(f T q_width / Q), h_max)) with q_width = sqrt(11);
@@ -107,6 +108,45 @@ inline double bisq(int64_t d, int64_t h) {
   return u * u;
 }
 
+// modified Bessel function I0 from its power series sum_k ((x/2)^k / k!)^2
+double bessel_i0(double x) {
+  const double q = 0.25 * x * x;
+  double term = 1.0, sum = 1.0;
+  for (int k = 1; k < 500; ++k) {
+    term *= q / ((double)k * (double)k);
+    sum += term;
+    if (term < 1e-17 * sum) break;
+  }
+  return sum;
+}
+
+// unnormalised window W'(d), |d| <= h, of the App. A family (u = |d|/h):
+// bisquare (1-u^2)^2; Hann (1+cos(pi u))/2; Kaiser I0(beta sqrt(1-u^2))/I0(beta);
+// Tukey and Planck-taper flat on u <= 1-a, tapering over the outer fraction a.
+// The Planck taper uses the continuous exponent Z = a/t - a/(a-t), t = 1-u.
+double window_profile(int64_t d, int64_t h, int win, double prm) {
+  const int64_t a = d < 0 ? -d : d;
+  if (a > h) return 0.0;
+  if (win == QTAM_WIN_BISQUARE) return bisq(d, h);
+  const double pi = 3.14159265358979323846;
+  const double u = (double)a / (double)h;
+  switch (win) {
+    case QTAM_WIN_HANN: return 0.5 * (1.0 + std::cos(pi * u));
+    case QTAM_WIN_KAISER: return bessel_i0(prm * std::sqrt(std::max(0.0, 1.0 - u * u))) / bessel_i0(prm);
+    case QTAM_WIN_TUKEY:
+      if (prm <= 0 || u <= 1.0 - prm) return 1.0;
+      return 0.5 * (1.0 + std::cos(pi * (u - (1.0 - prm)) / prm));
+    case QTAM_WIN_PLANCK: {
+      const double t = 1.0 - u;
+      if (t <= 0) return 0.0;
+      if (prm <= 0 || t >= prm) return 1.0;
+      const double z = prm / t - prm / (prm - t);
+      return 1.0 / (std::exp(std::min(700.0, std::max(-700.0, z))) + 1.0);
+    }
+    default: return 0.0;
+  }
+}
+
 struct MaskEntry {
   void* invP = nullptr;   // [Nr] T
   int* rows = nullptr;    // selected row indices
@@ -127,6 +167,8 @@ struct qtam_plan_s {
   int norm = QTAM_NORM_L2;
   double q_width = 0;
   double max_window_hz = 0;
+  int window = QTAM_WIN_BISQUARE;
+  double window_param = 0;
   int compute = QTAM_DTYPE_F32;
   int env = QTAM_DTYPE_F32;
   double tau = 0;
@@ -150,6 +192,7 @@ struct qtam_plan_s {
   void* d_twn = nullptr;
   void* d_twN = nullptr;
   void* d_tw4 = nullptr;
+  void* d_wtab = nullptr;   // W'(0..h) per distinct half-width, non-bisquare windows only
   size_t device_bytes = 0;
   std::map<int, void*> variant_tw;   // stage twiddle tables per row-kernel variant
   void* d_stw_col = nullptr;
@@ -163,6 +206,7 @@ struct qtam_plan_s {
     return env == QTAM_DTYPE_F64 ? 16 : (env == QTAM_DTYPE_F32 ? 8 : 4);
   }
   uint64_t all_mask() const { return P >= 64 ? ~0ull : ((1ull << P) - 1); }
+  double wprof(int64_t d, int64_t hk) const { return window_profile(d, hk, window, window_param); }
 };
 
 namespace {
@@ -231,7 +275,7 @@ qtam_status build_mask(qtam_plan_s* pl, uint64_t mask, MaskEntry** out) {
     for (int64_t d = -hk; d <= hk; ++d) {
       const int64_t fb = kc + d;
       if (fb < 0 || fb >= pl->Nr) continue;
-      wmax[fb] = std::max(wmax[fb], pl->c[r] * bisq(d, hk));
+      wmax[fb] = std::max(wmax[fb], pl->c[r] * pl->wprof(d, hk));
     }
   }
   for (int64_t f = 0; f < pl->Nr; ++f)
@@ -344,6 +388,23 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
     rows[r].inv_h2 = (T)(1.0 / ((double)pl->h[r] * (double)pl->h[r]));
     rows[r].kw_fwd = (T)(std::sqrt(pl->c[r] / sMN) / ((double)pl->h[r] * (double)pl->h[r]));
     rows[r].kw_inv = (T)(std::sqrt(pl->c[r] * sNM) / ((double)pl->h[r] * (double)pl->h[r]));
+    rows[r].woff = -1;
+  }
+  if (pl->window != QTAM_WIN_BISQUARE) {
+    // one W'(0..h) table per distinct half-width, read by the runtime engine
+    std::map<int, int> off;
+    std::vector<T> tab;
+    for (size_t r = 0; r < rows.size(); ++r) {
+      const int hk = pl->h[r];
+      auto it = off.find(hk);
+      if (it == off.end()) {
+        it = off.emplace(hk, (int)tab.size()).first;
+        for (int a = 0; a <= hk; ++a) tab.push_back((T)pl->wprof(a, hk));
+      }
+      rows[r].woff = it->second;
+    }
+    if (tab.size() > (size_t)INT32_MAX) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "window tables too large");
+    if ((s = upload(&pl->d_wtab, tab.data(), tab.size() * sizeof(T), tot)) != QTAM_OK) return s;
   }
   if ((s = upload(&pl->d_rows, rows.data(), rows.size() * sizeof(RowDev<T>), tot)) != QTAM_OK) return s;
   if (sizeof(T) == 4) {
@@ -380,6 +441,7 @@ void free_plan(qtam_plan_s* pl) {
     cudaFree(pl->d_twn);
     cudaFree(pl->d_twN);
     cudaFree(pl->d_tw4);
+    cudaFree(pl->d_wtab);
     cudaFree(pl->d_stw_col);
     cudaFree(pl->d_stw_row);
     for (auto& kv : pl->variant_tw) cudaFree(kv.second);
@@ -436,7 +498,8 @@ qtam_status run_spectrum(qtam_plan_s* pl, const void* x, int64_t B, void* X, voi
 template <typename T> qtam_status run_envelopes(qtam_plan_s* pl, const void* X, int64_t B, void* y, cudaStream_t st) {
   using V = cplx<T>;
   cudaError_t e = launch_rows_forward<T>(pl->rc, static_cast<const RowDev<T>*>(pl->d_rows), pl->P * pl->K, pl->Nr,
-                                         static_cast<const V*>(X), y, pl->env, B, static_cast<const V*>(pl->d_twM), st);
+                                         static_cast<const V*>(X), y, pl->env, B, static_cast<const V*>(pl->d_twM), st,
+                                         static_cast<const T*>(pl->d_wtab));
   return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "envelope launch");
 }
 
@@ -446,7 +509,8 @@ qtam_status run_accumulate(qtam_plan_s* pl, const void* y, int64_t B, const Mask
   cudaError_t e = cudaMemsetAsync(A, 0, (size_t)B * pl->Nr * sizeof(V), st);
   if (e != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync");
   e = launch_rows_inverse<T>(pl->rc, static_cast<const RowDev<T>*>(pl->d_rows), me->rows, me->n_sel, pl->P * pl->K,
-                             pl->Nr, y, pl->env, static_cast<V*>(A), B, static_cast<const V*>(pl->d_twM), st);
+                             pl->Nr, y, pl->env, static_cast<V*>(A), B, static_cast<const V*>(pl->d_twM), st,
+                             static_cast<const T*>(pl->d_wtab));
   return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "accumulate launch");
 }
 
@@ -502,7 +566,12 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   if (d->rows_per_plane < 1) return fail(QTAM_ERR_INVALID_ARG, "rows_per_plane >= 1 required");
   if (!(d->f_min > 0) || !(d->f_max >= d->f_min)) return fail(QTAM_ERR_INVALID_ARG, "0 < f_min <= f_max required");
   if (d->rows_per_plane > 1 && !(d->f_max > d->f_min)) return fail(QTAM_ERR_INVALID_ARG, "f_max > f_min required for K > 1");
-  if (d->window != QTAM_WIN_BISQUARE) return fail(QTAM_ERR_INVALID_ARG, "unknown window");
+  if (d->window < QTAM_WIN_BISQUARE || d->window > QTAM_WIN_PLANCK) return fail(QTAM_ERR_INVALID_ARG, "unknown window");
+  if (!std::isfinite(d->window_param)) return fail(QTAM_ERR_INVALID_ARG, "window_param must be finite");
+  if (d->window == QTAM_WIN_KAISER && !(d->window_param >= 0 && d->window_param <= 100))
+    return fail(QTAM_ERR_INVALID_ARG, "Kaiser beta must lie in [0, 100]");
+  if ((d->window == QTAM_WIN_TUKEY || d->window == QTAM_WIN_PLANCK) && !(d->window_param >= 0 && d->window_param <= 1))
+    return fail(QTAM_ERR_INVALID_ARG, "taper fraction must lie in [0, 1]");
   if (d->norm < QTAM_NORM_L2 || d->norm > QTAM_NORM_NONE) return fail(QTAM_ERR_INVALID_ARG, "unknown norm");
   if (d->compute_dtype != QTAM_DTYPE_F32 && d->compute_dtype != QTAM_DTYPE_F64) return fail(QTAM_ERR_INVALID_ARG, "compute_dtype must be F32 or F64");
   if (d->compute_dtype == QTAM_DTYPE_F64 && d->envelope_dtype != QTAM_DTYPE_F64) return fail(QTAM_ERR_INVALID_ARG, "F64 compute stores F64 envelopes");
@@ -522,6 +591,8 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->norm = d->norm;
   pl->q_width = d->q_width > 0 ? d->q_width : std::sqrt(11.0);
   pl->max_window_hz = d->max_window_hz;
+  pl->window = d->window;
+  pl->window_param = d->window == QTAM_WIN_HANN || d->window == QTAM_WIN_BISQUARE ? 0.0 : d->window_param;
   pl->compute = d->compute_dtype;
   pl->env = d->envelope_dtype;
   pl->tau = d->p_floor_rel >= 0 ? d->p_floor_rel : (pl->compute == QTAM_DTYPE_F64 ? 0.0 : 1e-6);
@@ -560,7 +631,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
       pl->h[r] = (int)hi;
       double s2 = 0;
       for (int64_t dd = -hi; dd <= hi; ++dd) {
-        const double w = bisq(dd, hi);
+        const double w = pl->wprof(dd, hi);
         s2 += w * w;
       }
       pl->c[r] = pl->norm == QTAM_NORM_L2 ? 1.0 / std::sqrt(s2) : (pl->norm == QTAM_NORM_PAPER ? 1.0 / s2 : 1.0);
@@ -591,7 +662,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
     for (int64_t dd = -hk; dd <= hk; ++dd) {
       const int64_t fb = kcr + dd;
       if (fb < 0 || fb >= pl->Nr) continue;
-      const double w = pl->c[r] * bisq(dd, hk);
+      const double w = pl->c[r] * pl->wprof(dd, hk);
       pl->Pplane[p][fb] += w * w;
       ++pl->band_bins;
     }
@@ -606,7 +677,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.threads = threads_for(pl->rc.rp, 0);
   pl->rc.smem = smem_for(pl->rc.rp, 0, pl->cplx_size());
   pl->rc.variant = -1;
-  if (!dbl) {
+  if (!dbl && pl->window == QTAM_WIN_BISQUARE) {   // compile-time variants hard-code the bisquare
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) {
         pl->rc.variant = v;   // first registered variant for this length
@@ -691,7 +762,7 @@ qtam_status qtam_plan_variants(qtam_plan_t pl, int32_t* ids, int32_t capacity, i
     ++n;
   };
   push(-1);
-  if (pl->compute == QTAM_DTYPE_F32)
+  if (pl->compute == QTAM_DTYPE_F32 && pl->window == QTAM_WIN_BISQUARE)
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) push(v);
   *count = n;
@@ -702,8 +773,8 @@ qtam_status qtam_plan_set_variant(qtam_plan_t pl, int32_t id) {
   if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
   if (id != -1) {
     const RowVariant* v = row_variant(id);
-    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32)
-      return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length or dtype");
+    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || pl->window != QTAM_WIN_BISQUARE)
+      return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length, dtype or window");
   }
   if (id >= 0 && pl->device >= 0) {
     auto it = pl->variant_tw.find(id);

@@ -30,6 +30,7 @@ template <typename T> struct RowDev {
   T inv_h2;   // 1 / h^2
   T kw_fwd;   // sqrt(c_fwd) / h^2: window weight c_fwd W'(d) = (kw_fwd (h^2 - d^2))^2
   T kw_inv;   // sqrt(c_inv) / h^2
+  int woff;   // offset of this row's W'(0..h) in the plan's window table; -1: bisquare formula
 };
 
 // Long real FFT of N = 2n samples as an n = n1 * n2 four-step complex FFT.
@@ -96,12 +97,13 @@ cudaError_t launch_synthesis(const LongCfg& c, const cplx<T>* A, const T* invP, 
 // X: [B][Nr] spectrum -> y: [B][R][M] envelopes (R = P*K rows)
 template <typename T>
 cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_rows, int64_t Nr, const cplx<T>* X,
-                                void* y, int env, int64_t B, const cplx<T>* twM, cudaStream_t st);
+                                void* y, int env, int64_t B, const cplx<T>* twM, cudaStream_t st,
+                                const T* wtab = nullptr);
 // y rows listed in row_list -> atomically accumulated into A: [B][Nr] (must be zeroed)
 template <typename T>
 cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const int* row_list, int n_sel, int n_rows,
                                 int64_t Nr, const void* y, int env, cplx<T>* A, int64_t B, const cplx<T>* twM,
-                                cudaStream_t st);
+                                cudaStream_t st, const T* wtab = nullptr);
 
 // radix sequence of the static long-FFT engine used for a pass of length m
 // with 2^nbs interleaved transforms (FP32); false when the runtime engine runs

@@ -27,6 +27,7 @@ STATUS = {
     8: "QTAM_ERR_NO_DEVICE", 9: "QTAM_ERR_WORKSPACE",
 }
 NORM = {"l2": 0, "paper": 1, "none": 2}
+WINDOW = {"bisquare": 0, "hann": 1, "kaiser": 2, "tukey": 3, "planck": 4}
 DTYPE = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
 ENV_BYTES = {"f32": 8, "f64": 16, "bf16": 4, "f16": 4}
 
@@ -44,6 +45,7 @@ class qtam_plan_desc(ctypes.Structure):
         ("rows_per_plane", ctypes.c_int32), ("window", ctypes.c_int32), ("norm", ctypes.c_int32),
         ("q_width", ctypes.c_double), ("max_window_hz", ctypes.c_double), ("n_out", ctypes.c_int32),
         ("compute_dtype", ctypes.c_int32), ("envelope_dtype", ctypes.c_int32), ("p_floor_rel", ctypes.c_double),
+        ("window_param", ctypes.c_double),
     ]
 
 
@@ -148,7 +150,7 @@ def _stream(stream) -> int | None:
 # C-named entry points (thin marshalling)
 # ----------------------------------------------------------------------------
 def make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", q_width=0.0, max_window_hz=0.0,
-              n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0):
+              n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0, window="bisquare", window_param=0.0):
     d = qtam_plan_desc()
     lib().qtam_plan_desc_init(ctypes.byref(d))
     qarr = (ctypes.c_double * len(qs))(*[float(q) for q in qs])
@@ -165,6 +167,8 @@ def make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", 
     d.compute_dtype = DTYPE[compute]
     d.envelope_dtype = DTYPE[envelope or compute]
     d.p_floor_rel = float(p_floor_rel)
+    d.window = WINDOW[window]
+    d.window_param = float(window_param)
     d._keep = qarr  # keep the Q array alive with the struct
     return d
 
@@ -340,12 +344,13 @@ class Plan:
     """
 
     def __init__(self, sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", q_width=0.0,
-                 max_window_hz=0.0, n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0, device=0):
+                 max_window_hz=0.0, n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0, device=0,
+                 window="bisquare", window_param=0.0):
         self.compute = compute
         self.envelope = envelope or compute
         self.device = int(device)
         self._desc = make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm, q_width, max_window_hz,
-                               n_out, compute, self.envelope, p_floor_rel)
+                               n_out, compute, self.envelope, p_floor_rel, window, window_param)
         self.handle = qtam_plan(self._desc, self.device)
         self.info = qtam_plan_info(self.handle)
         self.N = self.info["length"]

@@ -38,11 +38,21 @@ CASES = [
     dict(fs=64.0, N=512, qs=(2.0,), fmin=3.0, fmax=32.0, K=7, norm="none", max_window_hz=2.0),
     dict(fs=256.0, N=1024, qs=(6.0, 12.0), fmin=2.0, fmax=100.0, K=20, n_out=96),
     dict(fs=16384, N=16384 * 2, qs=(8, 16, 32), fmin=20, fmax=2048, K=128),
+    # the App. A window family
+    dict(fs=4096, N=32768, qs=(8, 16, 32), fmin=20, fmax=2048, K=128, window="hann"),
+    dict(fs=4096, N=32768, qs=(8, 16, 32), fmin=20, fmax=2048, K=128, window="kaiser", window_param=8.0),
+    dict(fs=64.0, N=512, qs=(4.0, 8.0), fmin=3.0, fmax=30.0, K=12, window="tukey", window_param=0.5),
+    dict(fs=64.0, N=512, qs=(4.0, 8.0), fmin=3.0, fmax=30.0, K=12, window="planck", window_param=0.3,
+         norm="paper"),
+    dict(fs=4096, N=16384, qs=(8,), fmin=20, fmax=1024, K=64, window="tukey", window_param=1.0),
+    dict(fs=4096, N=16384, qs=(8,), fmin=20, fmax=1024, K=64, window="planck", window_param=0.0),
+    dict(fs=4096, N=16384, qs=(8,), fmin=20, fmax=1024, K=64, window="kaiser", window_param=0.0),
 ]
 
 
 def _both(c):
-    kw = dict(norm=c.get("norm", "l2"), max_window_hz=c.get("max_window_hz", 0.0), n_out=c.get("n_out", 0))
+    kw = dict(norm=c.get("norm", "l2"), max_window_hz=c.get("max_window_hz", 0.0), n_out=c.get("n_out", 0),
+              window=c.get("window", "bisquare"), window_param=c.get("window_param", 0.0))
     g = O.geometry(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], **kw)
     p = qtam.Plan(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], device=-1, **kw)
     return g, p
@@ -102,6 +112,22 @@ def test_argument_errors():
     assert _err(lambda: qtam.qtam_forward(p.handle, 0, 1, 0, 0, 0, 0)) == 8    # host-only plan
     assert _err(lambda: qtam.qtam_frame_operator(p.handle, 0b110, p.Nr)) == 1  # plane 1, 2 do not exist
     assert _err(lambda: qtam.qtam_workspace_size(p.handle, -1)) == 1
+
+
+def test_window_argument_errors_and_variants():
+    base = (4096, 16384, (8,), 20, 1024, 64)
+    assert _err(lambda: qtam.Plan(*base, window="kaiser", window_param=-1.0, device=-1)) == 1
+    assert _err(lambda: qtam.Plan(*base, window="tukey", window_param=1.5, device=-1)) == 1
+    assert _err(lambda: qtam.Plan(*base, window="planck", window_param=float("nan"), device=-1)) == 1
+    d = qtam.make_desc(*base)
+    d.window = 7
+    assert _err(lambda: qtam.qtam_plan(d, -1)) == 1
+    # compile-time row variants hard-code the bisquare: other windows run the runtime engine only
+    b = qtam.Plan(4096.0, 262144, (4, 8, 16, 32, 64), 20.0, 2048.0, 128, device=-1)
+    h = qtam.Plan(4096.0, 262144, (4, 8, 16, 32, 64), 20.0, 2048.0, 128, window="hann", device=-1)
+    assert len(qtam.qtam_plan_variants(b.handle)) > 1 and b.info["row_variant"] >= 0
+    assert qtam.qtam_plan_variants(h.handle) == [-1] and h.info["row_variant"] == -1
+    assert _err(lambda: qtam.qtam_plan_set_variant(h.handle, qtam.qtam_plan_variants(b.handle)[1])) == 1
 
 
 def test_f64_defaults():

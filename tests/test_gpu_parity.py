@@ -55,7 +55,8 @@ def elem_ok(a, b, tol):
 def geom_of(p):
     return O.geometry(p._args["fs"], p._args["N"], p._args["qs"], p._args["fmin"], p._args["fmax"], p._args["K"],
                       norm=p._args.get("norm", "l2"), max_window_hz=p._args.get("max_window_hz", 0.0),
-                      n_out=p._args.get("n_out", 0))
+                      n_out=p._args.get("n_out", 0), window=p._args.get("window", "bisquare"),
+                      window_param=p._args.get("window_param", 0.0))
 
 
 def make(fs, N, qs, fmin, fmax, K, compute="f32", envelope=None, **kw):
@@ -139,6 +140,66 @@ def test_forward_and_roundtrip_small(i):
         assert rel(Yg[b], ref) < FWD_FROB["f32"]
         assert elem_ok(Yg[b], ref, FWD_ELEM["f32"])
         assert rel(xh[b], O.projection(g, xb, tau=tau)) < RT["f32"]
+
+
+WINDOWS = [("hann", 0.0), ("kaiser", 8.0), ("tukey", 0.5), ("planck", 0.3)]
+
+
+@pytest.mark.parametrize("win,prm", WINDOWS)
+@pytest.mark.parametrize("i", [0, 1, 2, 4])
+def test_window_family_forward_and_roundtrip(win, prm, i):
+    """App. A's alternative windows: per-plan W' tables read by the runtime engine."""
+    p = make(**SMALL[i], window=win, window_param=prm)
+    assert p.info["row_variant"] == -1
+    g = geom_of(p)
+    B = 2
+    x = np.stack([synth.white(700 + 10 * i + b, g.N) for b in range(B)]).astype(np.float32)
+    y = p.forward(dev(x))
+    Yg = env_np(p, y)
+    xh = host(p.inverse(y)).astype(np.float64)
+    tau = p.info["p_floor_rel"]
+    for b in range(B):
+        xb = x[b].astype(np.float64)
+        ref = O.forward(g, xb)
+        assert rel(Yg[b], ref) < FWD_FROB["f32"]
+        assert elem_ok(Yg[b], ref, FWD_ELEM["f32"])
+        assert rel(xh[b], O.projection(g, xb, tau=tau)) < RT["f32"]
+
+
+@pytest.mark.parametrize("win,prm", WINDOWS)
+def test_window_family_float64(win, prm):
+    """FP64 with an explicit floor tau = 1e-10: the Planck taper's edge weights
+    fall like exp(-a h), so without a floor its frame operator keeps bins with
+    P ~ 1e-32 max P and the canonical inverse divides rounding noise by them."""
+    tau = 1e-10
+    p = make(4096.0, 16384, (8.0,), 20.0, 1024.0, 64, compute="f64", window=win, window_param=prm, p_floor_rel=tau)
+    g = geom_of(p)
+    assert p.info["kept_bins"] == int(O.kept_bins(O.frame_operator(g), tau).sum())
+    x = synth.white_sine_gaussian_segment(3).astype(np.float64)
+    y = p.forward(dev(x[None]))
+    Y = env_np(p, y)[0]
+    ref = O.forward(g, x)
+    assert rel(Y, ref) < FWD_FROB["f64"]
+    assert elem_ok(Y, ref, FWD_ELEM["f64"])
+    assert rel(host(p.inverse(y))[0], O.projection(g, x, tau=tau)) < RT["f64"]
+
+
+def test_window_family_full_size_sampled_rows():
+    """64 s, five planes, 128 rows, Kaiser beta = 8 (M = 4800, runtime engine)."""
+    p = make(4096.0, 262144, (4.0, 8.0, 16.0, 32.0, 64.0), 20.0, 2048.0, 128, window="kaiser", window_param=8.0)
+    g = geom_of(p)
+    x = synth.coloured_chirp_segment(5)[None]
+    y = p.forward(dev(x))
+    Y = env_np(p, y)[0]
+    X = O.spectrum(x[0].astype(np.float64))
+    rows = [(0, 0), (0, 127), (1, 64), (3, 100), (4, 127)]
+    big = max(np.max(np.abs(O.forward_row(g, X, a, k))) for a, k in rows)
+    for a, k in rows:
+        ref = O.forward_row(g, X, a, k)
+        assert rel(Y[a, k], ref) < FWD_FROB["f32"], (a, k)
+        assert np.max(np.abs(Y[a, k] - ref)) <= FWD_ELEM["f32"] * big
+    xh = host(p.inverse(y))[0].astype(np.float64)
+    assert rel(xh, O.projection(g, x[0].astype(np.float64), tau=p.info["p_floor_rel"])) < RT["f32"]
 
 
 def test_batch_zero_is_noop():
