@@ -99,6 +99,12 @@ typedef struct {
   double p_floor_rel;     /* tau; < 0 selects the default (1e-6 for F32, 0 for F64) */
   double window_param;    /* Kaiser beta in [0, 100]; Tukey / Planck taper fraction in [0, 1];
                              ignored for bisquare and Hann; anything else -> QTAM_ERR_INVALID_ARG */
+  /* composite bank (App. A: planes scan Q x window x shape parameter): when
+   * non-NULL, n_q entries giving plane p's window / parameter, overriding
+   * `window` / `window_param` (same rules per entry).  Read during qtam_plan
+   * only; the caller keeps ownership.  Planes may repeat a Q value. */
+  const int32_t* plane_window;
+  const double* plane_window_param;
 } qtam_plan_desc;
 
 typedef struct {

@@ -99,9 +99,16 @@ class Geometry:
     kc: np.ndarray          # [P, K] centre bins
     h: np.ndarray           # [P, K] half-widths
     c: np.ndarray           # [P, K] window normalisation c_k
-    window: str = "bisquare"
-    window_param: float = 0.0
+    window: object = "bisquare"       # one name, or one per plane (composite bank)
+    window_param: object = 0.0        # one value, or one per plane
     extra: dict = field(default_factory=dict)
+
+    def plane_window(self, p: int):
+        """(window name, shape parameter) of plane p: a plane of the bank is a
+        (Q, window, parameter) configuration (App. A, composite filter bank)."""
+        w = self.window if isinstance(self.window, str) else self.window[p]
+        a = self.window_param if np.ndim(self.window_param) == 0 else self.window_param[p]
+        return w, float(a)
 
     @property
     def P(self) -> int:
@@ -219,6 +226,10 @@ def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
     else:
         h_max = int(math.ceil(T * df_max)) // 2
     P = len(qs)
+    if not isinstance(window, str) and len(window) != P:
+        raise ValueError("one window per plane is required")
+    if np.ndim(window_param) != 0 and len(window_param) != P:
+        raise ValueError("one window parameter per plane is required")
     f = np.zeros((P, K))
     kc = np.zeros((P, K), dtype=np.int64)
     h = np.zeros((P, K), dtype=np.int64)
@@ -229,7 +240,9 @@ def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
             kc[p, k] = round_half_away(grid[k] * T)
             h_ideal = int(math.floor(grid[k] * T * q_width / Q))
             h[p, k] = max(1, min(h_ideal, h_max))
-            c[p, k] = window_norm(int(h[p, k]), norm, window, window_param)
+            wname = window if isinstance(window, str) else window[p]
+            wpar = window_param if np.ndim(window_param) == 0 else window_param[p]
+            c[p, k] = window_norm(int(h[p, k]), norm, wname, float(wpar))
     Lmax = int(np.max(2 * h + 1))
     if n_out:
         if n_out < Lmax:
@@ -239,14 +252,16 @@ def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
         M = smooth_length(Lmax)
     return Geometry(fs=float(fs), N=N, qs=tuple(float(q) for q in qs), fmin=float(fmin),
                     fmax=float(fmax), K=int(K), norm=norm, q_width=float(q_width),
-                    h_max=int(h_max), M=M, f=f, kc=kc, h=h, c=c, window=window,
-                    window_param=float(window_param))
+                    h_max=int(h_max), M=M, f=f, kc=kc, h=h, c=c,
+                    window=window if isinstance(window, str) else tuple(window),
+                    window_param=float(window_param) if np.ndim(window_param) == 0
+                    else tuple(float(a) for a in window_param))
 
 
 def window(g: Geometry, p: int, k: int) -> np.ndarray:
     """Dense W_k[f], f = 0..N/2, truncated to the one-sided band (reading C6)."""
     fbin = np.arange(g.Nr)
-    return g.c[p, k] * window_profile(fbin - g.kc[p, k], int(g.h[p, k]), g.window, g.window_param)
+    return g.c[p, k] * window_profile(fbin - g.kc[p, k], int(g.h[p, k]), *g.plane_window(p))
 
 
 def frame_operator(g: Geometry, planes=None) -> np.ndarray:
@@ -292,7 +307,7 @@ def forward_row(g: Geometry, X: np.ndarray, p: int, k: int) -> np.ndarray:
     """
     d, fb = band(g, p, k)
     Z = np.zeros(g.M, dtype=np.complex128)
-    w = g.c[p, k] * window_profile(d, int(g.h[p, k]), g.window, g.window_param)
+    w = g.c[p, k] * window_profile(d, int(g.h[p, k]), *g.plane_window(p))
     Z[d % g.M] = w * X[fb]
     return np.fft.ifft(Z) * math.sqrt(g.M / g.N)
 
@@ -320,7 +335,7 @@ def accumulate(g: Geometry, Y: np.ndarray, planes=None) -> np.ndarray:
         for k in range(g.K):
             S = np.fft.fft(Y[p, k]) * math.sqrt(g.N / g.M)
             d, fb = band(g, p, k)
-            w = g.c[p, k] * window_profile(d, int(g.h[p, k]), g.window, g.window_param)
+            w = g.c[p, k] * window_profile(d, int(g.h[p, k]), *g.plane_window(p))
             A[fb] += w * S[d % g.M]
     return A
 

@@ -25,6 +25,7 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "../../include/qtam.h"
@@ -167,8 +168,8 @@ struct qtam_plan_s {
   int norm = QTAM_NORM_L2;
   double q_width = 0;
   double max_window_hz = 0;
-  int window = QTAM_WIN_BISQUARE;
-  double window_param = 0;
+  std::vector<int> window;          // per plane (QTAM_WIN_*)
+  std::vector<double> window_param; // per plane
   int compute = QTAM_DTYPE_F32;
   int env = QTAM_DTYPE_F32;
   double tau = 0;
@@ -206,7 +207,12 @@ struct qtam_plan_s {
     return env == QTAM_DTYPE_F64 ? 16 : (env == QTAM_DTYPE_F32 ? 8 : 4);
   }
   uint64_t all_mask() const { return P >= 64 ? ~0ull : ((1ull << P) - 1); }
-  double wprof(int64_t d, int64_t hk) const { return window_profile(d, hk, window, window_param); }
+  double wprof(int64_t d, int64_t hk, int p) const { return window_profile(d, hk, window[p], window_param[p]); }
+  bool all_bisquare() const {
+    for (int w : window)
+      if (w != QTAM_WIN_BISQUARE) return false;
+    return true;
+  }
 };
 
 namespace {
@@ -275,7 +281,7 @@ qtam_status build_mask(qtam_plan_s* pl, uint64_t mask, MaskEntry** out) {
     for (int64_t d = -hk; d <= hk; ++d) {
       const int64_t fb = kc + d;
       if (fb < 0 || fb >= pl->Nr) continue;
-      wmax[fb] = std::max(wmax[fb], pl->c[r] * pl->wprof(d, hk));
+      wmax[fb] = std::max(wmax[fb], pl->c[r] * pl->wprof(d, hk, r / pl->K));
     }
   }
   for (int64_t f = 0; f < pl->Nr; ++f)
@@ -390,20 +396,23 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
     rows[r].kw_inv = (T)(std::sqrt(pl->c[r] * sNM) / ((double)pl->h[r] * (double)pl->h[r]));
     rows[r].woff = -1;
   }
-  if (pl->window != QTAM_WIN_BISQUARE) {
-    // one W'(0..h) table per distinct half-width, read by the runtime engine
-    std::map<int, int> off;
+  if (!pl->all_bisquare()) {
+    // one W'(0..h) table per distinct (window, parameter, half-width), read by
+    // the runtime engine; bisquare rows of a mixed bank keep the formula
+    std::map<std::tuple<int, double, int>, int> off;
     std::vector<T> tab;
     for (size_t r = 0; r < rows.size(); ++r) {
-      const int hk = pl->h[r];
-      auto it = off.find(hk);
+      const int p = (int)r / pl->K, hk = pl->h[r];
+      if (pl->window[p] == QTAM_WIN_BISQUARE) continue;
+      const auto key = std::make_tuple(pl->window[p], pl->window_param[p], hk);
+      auto it = off.find(key);
       if (it == off.end()) {
-        it = off.emplace(hk, (int)tab.size()).first;
-        for (int a = 0; a <= hk; ++a) tab.push_back((T)pl->wprof(a, hk));
+        if (tab.size() + hk + 1 > (size_t)INT32_MAX) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "window tables too large");
+        it = off.emplace(key, (int)tab.size()).first;
+        for (int a = 0; a <= hk; ++a) tab.push_back((T)pl->wprof(a, hk, p));
       }
       rows[r].woff = it->second;
     }
-    if (tab.size() > (size_t)INT32_MAX) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "window tables too large");
     if ((s = upload(&pl->d_wtab, tab.data(), tab.size() * sizeof(T), tot)) != QTAM_OK) return s;
   }
   if ((s = upload(&pl->d_rows, rows.data(), rows.size() * sizeof(RowDev<T>), tot)) != QTAM_OK) return s;
@@ -566,12 +575,15 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   if (d->rows_per_plane < 1) return fail(QTAM_ERR_INVALID_ARG, "rows_per_plane >= 1 required");
   if (!(d->f_min > 0) || !(d->f_max >= d->f_min)) return fail(QTAM_ERR_INVALID_ARG, "0 < f_min <= f_max required");
   if (d->rows_per_plane > 1 && !(d->f_max > d->f_min)) return fail(QTAM_ERR_INVALID_ARG, "f_max > f_min required for K > 1");
-  if (d->window < QTAM_WIN_BISQUARE || d->window > QTAM_WIN_PLANCK) return fail(QTAM_ERR_INVALID_ARG, "unknown window");
-  if (!std::isfinite(d->window_param)) return fail(QTAM_ERR_INVALID_ARG, "window_param must be finite");
-  if (d->window == QTAM_WIN_KAISER && !(d->window_param >= 0 && d->window_param <= 100))
-    return fail(QTAM_ERR_INVALID_ARG, "Kaiser beta must lie in [0, 100]");
-  if ((d->window == QTAM_WIN_TUKEY || d->window == QTAM_WIN_PLANCK) && !(d->window_param >= 0 && d->window_param <= 1))
-    return fail(QTAM_ERR_INVALID_ARG, "taper fraction must lie in [0, 1]");
+  for (int i = 0; i < d->n_q; ++i) {
+    const int w = d->plane_window ? d->plane_window[i] : d->window;
+    const double a = d->plane_window_param ? d->plane_window_param[i] : d->window_param;
+    if (w < QTAM_WIN_BISQUARE || w > QTAM_WIN_PLANCK) return fail(QTAM_ERR_INVALID_ARG, "unknown window");
+    if (!std::isfinite(a)) return fail(QTAM_ERR_INVALID_ARG, "window_param must be finite");
+    if (w == QTAM_WIN_KAISER && !(a >= 0 && a <= 100)) return fail(QTAM_ERR_INVALID_ARG, "Kaiser beta must lie in [0, 100]");
+    if ((w == QTAM_WIN_TUKEY || w == QTAM_WIN_PLANCK) && !(a >= 0 && a <= 1))
+      return fail(QTAM_ERR_INVALID_ARG, "taper fraction must lie in [0, 1]");
+  }
   if (d->norm < QTAM_NORM_L2 || d->norm > QTAM_NORM_NONE) return fail(QTAM_ERR_INVALID_ARG, "unknown norm");
   if (d->compute_dtype != QTAM_DTYPE_F32 && d->compute_dtype != QTAM_DTYPE_F64) return fail(QTAM_ERR_INVALID_ARG, "compute_dtype must be F32 or F64");
   if (d->compute_dtype == QTAM_DTYPE_F64 && d->envelope_dtype != QTAM_DTYPE_F64) return fail(QTAM_ERR_INVALID_ARG, "F64 compute stores F64 envelopes");
@@ -591,8 +603,12 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->norm = d->norm;
   pl->q_width = d->q_width > 0 ? d->q_width : std::sqrt(11.0);
   pl->max_window_hz = d->max_window_hz;
-  pl->window = d->window;
-  pl->window_param = d->window == QTAM_WIN_HANN || d->window == QTAM_WIN_BISQUARE ? 0.0 : d->window_param;
+  for (int i = 0; i < d->n_q; ++i) {
+    const int w = d->plane_window ? d->plane_window[i] : d->window;
+    const double a = d->plane_window_param ? d->plane_window_param[i] : d->window_param;
+    pl->window.push_back(w);
+    pl->window_param.push_back(w == QTAM_WIN_HANN || w == QTAM_WIN_BISQUARE ? 0.0 : a);
+  }
   pl->compute = d->compute_dtype;
   pl->env = d->envelope_dtype;
   pl->tau = d->p_floor_rel >= 0 ? d->p_floor_rel : (pl->compute == QTAM_DTYPE_F64 ? 0.0 : 1e-6);
@@ -631,7 +647,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
       pl->h[r] = (int)hi;
       double s2 = 0;
       for (int64_t dd = -hi; dd <= hi; ++dd) {
-        const double w = pl->wprof(dd, hi);
+        const double w = pl->wprof(dd, hi, p);
         s2 += w * w;
       }
       pl->c[r] = pl->norm == QTAM_NORM_L2 ? 1.0 / std::sqrt(s2) : (pl->norm == QTAM_NORM_PAPER ? 1.0 / s2 : 1.0);
@@ -662,7 +678,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
     for (int64_t dd = -hk; dd <= hk; ++dd) {
       const int64_t fb = kcr + dd;
       if (fb < 0 || fb >= pl->Nr) continue;
-      const double w = pl->c[r] * pl->wprof(dd, hk);
+      const double w = pl->c[r] * pl->wprof(dd, hk, p);
       pl->Pplane[p][fb] += w * w;
       ++pl->band_bins;
     }
@@ -677,7 +693,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.threads = threads_for(pl->rc.rp, 0);
   pl->rc.smem = smem_for(pl->rc.rp, 0, pl->cplx_size());
   pl->rc.variant = -1;
-  if (!dbl && pl->window == QTAM_WIN_BISQUARE) {   // compile-time variants hard-code the bisquare
+  if (!dbl && pl->all_bisquare()) {   // compile-time variants hard-code the bisquare
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) {
         pl->rc.variant = v;   // first registered variant for this length
@@ -762,7 +778,7 @@ qtam_status qtam_plan_variants(qtam_plan_t pl, int32_t* ids, int32_t capacity, i
     ++n;
   };
   push(-1);
-  if (pl->compute == QTAM_DTYPE_F32 && pl->window == QTAM_WIN_BISQUARE)
+  if (pl->compute == QTAM_DTYPE_F32 && pl->all_bisquare())
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) push(v);
   *count = n;
@@ -773,7 +789,7 @@ qtam_status qtam_plan_set_variant(qtam_plan_t pl, int32_t id) {
   if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
   if (id != -1) {
     const RowVariant* v = row_variant(id);
-    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || pl->window != QTAM_WIN_BISQUARE)
+    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || !pl->all_bisquare())
       return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length, dtype or window");
   }
   if (id >= 0 && pl->device >= 0) {

@@ -45,7 +45,8 @@ class qtam_plan_desc(ctypes.Structure):
         ("rows_per_plane", ctypes.c_int32), ("window", ctypes.c_int32), ("norm", ctypes.c_int32),
         ("q_width", ctypes.c_double), ("max_window_hz", ctypes.c_double), ("n_out", ctypes.c_int32),
         ("compute_dtype", ctypes.c_int32), ("envelope_dtype", ctypes.c_int32), ("p_floor_rel", ctypes.c_double),
-        ("window_param", ctypes.c_double),
+        ("window_param", ctypes.c_double), ("plane_window", ctypes.POINTER(ctypes.c_int32)),
+        ("plane_window_param", ctypes.POINTER(ctypes.c_double)),
     ]
 
 
@@ -167,9 +168,24 @@ def make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", 
     d.compute_dtype = DTYPE[compute]
     d.envelope_dtype = DTYPE[envelope or compute]
     d.p_floor_rel = float(p_floor_rel)
-    d.window = WINDOW[window]
-    d.window_param = float(window_param)
-    d._keep = qarr  # keep the Q array alive with the struct
+    keep = [qarr]  # arrays the struct points to live as long as the struct
+    if isinstance(window, str):
+        d.window = WINDOW[window]
+    else:                      # composite bank: one window per plane
+        warr = (ctypes.c_int32 * len(window))(*[WINDOW[w] for w in window])
+        d.plane_window = ctypes.cast(warr, ctypes.POINTER(ctypes.c_int32))
+        keep.append(warr)
+        if len(window) != len(qs):
+            raise ValueError("one window per plane is required")
+    if np.ndim(window_param) == 0:
+        d.window_param = float(window_param)
+    else:
+        parr = (ctypes.c_double * len(window_param))(*[float(a) for a in window_param])
+        d.plane_window_param = ctypes.cast(parr, ctypes.POINTER(ctypes.c_double))
+        keep.append(parr)
+        if len(window_param) != len(qs):
+            raise ValueError("one window parameter per plane is required")
+    d._keep = keep
     return d
 
 

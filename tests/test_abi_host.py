@@ -47,6 +47,9 @@ CASES = [
     dict(fs=4096, N=16384, qs=(8,), fmin=20, fmax=1024, K=64, window="tukey", window_param=1.0),
     dict(fs=4096, N=16384, qs=(8,), fmin=20, fmax=1024, K=64, window="planck", window_param=0.0),
     dict(fs=4096, N=16384, qs=(8,), fmin=20, fmax=1024, K=64, window="kaiser", window_param=0.0),
+    # composite bank: planes scan Q x window x parameter
+    dict(fs=4096, N=32768, qs=(8, 8, 8, 16, 16), fmin=20, fmax=2048, K=128,
+         window=("bisquare", "tukey", "kaiser", "planck", "hann"), window_param=(0.0, 0.5, 6.0, 0.3, 0.0)),
 ]
 
 
@@ -128,6 +131,14 @@ def test_window_argument_errors_and_variants():
     assert len(qtam.qtam_plan_variants(b.handle)) > 1 and b.info["row_variant"] >= 0
     assert qtam.qtam_plan_variants(h.handle) == [-1] and h.info["row_variant"] == -1
     assert _err(lambda: qtam.qtam_plan_set_variant(h.handle, qtam.qtam_plan_variants(b.handle)[1])) == 1
+    # a bank with one non-bisquare plane also runs the runtime engine only
+    m = qtam.Plan(4096.0, 262144, (4, 8), 20.0, 2048.0, 128, window=("bisquare", "tukey"), window_param=(0, 0.5),
+                  device=-1)
+    assert qtam.qtam_plan_variants(m.handle) == [-1]
+    assert _err(lambda: qtam.Plan(*base[:2], (8, 16), *base[3:], window=("hann", "tukey"),
+                                  window_param=(0.0, 2.0), device=-1)) == 1
+    with pytest.raises(ValueError):
+        qtam.Plan(*base[:2], (8, 16), *base[3:], window=("hann",), device=-1)
 
 
 def test_f64_defaults():

@@ -184,6 +184,30 @@ def test_window_family_float64(win, prm):
     assert rel(host(p.inverse(y))[0], O.projection(g, x, tau=tau)) < RT["f64"]
 
 
+def test_composite_bank_forward_roundtrip_and_optimal_plane():
+    """Planes scanning Q x window x parameter in one plan (bisquare planes keep the
+    formula, the others read their tables), one launch per stage."""
+    wins = ("bisquare", "tukey", "kaiser", "planck", "hann", "bisquare")
+    prms = (0.0, 0.5, 6.0, 0.3, 0.0, 0.0)
+    p = make(4096.0, 32768, (8.0, 8.0, 8.0, 16.0, 16.0, 32.0), 20.0, 2048.0, 128, window=wins, window_param=prms)
+    g = geom_of(p)
+    x = np.stack([synth.glitchy_segment(900 + b, g.N, 4096.0, chirp=(b == 0)) for b in range(2)]).astype(np.float32)
+    y = p.forward(dev(x))
+    Yg = env_np(p, y)
+    xh = host(p.inverse(y)).astype(np.float64)
+    e, pk, _, _ = p.plane_metrics(y)
+    tau = p.info["p_floor_rel"]
+    for b in range(2):
+        xb = x[b].astype(np.float64)
+        ref = O.forward(g, xb)
+        assert rel(Yg[b], ref) < FWD_FROB["f32"]
+        assert elem_ok(Yg[b], ref, FWD_ELEM["f32"])
+        assert rel(xh[b], O.projection(g, xb, tau=tau)) < RT["f32"]
+        eo, po, _, _ = O.plane_metrics(ref)
+        assert np.allclose(host(e)[b], eo, rtol=2e-6)
+        assert np.allclose(host(pk)[b], po, rtol=5e-6)
+
+
 def test_window_family_full_size_sampled_rows():
     """64 s, five planes, 128 rows, Kaiser beta = 8 (M = 4800, runtime engine)."""
     p = make(4096.0, 262144, (4.0, 8.0, 16.0, 32.0, 64.0), 20.0, 2048.0, 128, window="kaiser", window_param=8.0)

@@ -421,3 +421,31 @@ def test_window_family_frame_identities(window, param):
             hk = int(g.h[p, k])
             w = g.c[p, k] * O.window_profile(np.arange(-hk, hk + 1), hk, window, param)
             assert np.sum(w ** 2) == pytest.approx(1.0, rel=1e-12)
+
+
+def test_composite_bank_planes_are_single_window_transforms():
+    """A plane of the composite bank (App. A: Q x window x parameter) is the
+    one-plane transform with that plane's configuration; the bank's frame
+    operator is the sum of its planes' operators, and the bank inverts to the
+    projection onto its kept bins."""
+    qs = (4.0, 4.0, 8.0, 8.0)
+    wins = ("bisquare", "tukey", "kaiser", "planck")
+    prms = (0.0, 0.5, 6.0, 0.3)
+    g = O.geometry(64.0, 512, qs, 3.0, 30.0, 12, window=wins, window_param=prms)
+    x = _rand_x(g.N, 44)
+    Y = O.forward(g, x)
+    Pf = np.zeros(g.Nr)
+    for p in range(g.P):
+        g1 = O.geometry(64.0, 512, (qs[p],), 3.0, 30.0, 12, window=wins[p], window_param=prms[p], n_out=g.M)
+        assert g.plane_window(p) == (wins[p], prms[p])
+        assert np.array_equal(g1.h[0], g.h[p]) and np.allclose(g1.c[0], g.c[p], rtol=1e-15)
+        assert np.allclose(O.forward(g1, x)[0], Y[p], rtol=0, atol=1e-14 * np.max(np.abs(Y)))
+        Pf += O.frame_operator(g1)
+    assert np.allclose(O.frame_operator(g), Pf, rtol=1e-14, atol=0)
+    assert np.linalg.norm(O.inverse(g, Y) - O.projection(g, x)) < 1e-12 * np.linalg.norm(x)
+    # the same name on every plane equals the single-window geometry
+    gs = O.geometry(64.0, 512, qs, 3.0, 30.0, 12, window="hann")
+    gb = O.geometry(64.0, 512, qs, 3.0, 30.0, 12, window=("hann",) * 4, window_param=(0.0,) * 4)
+    assert np.array_equal(gs.c, gb.c) and np.allclose(O.forward(gs, x), O.forward(gb, x), rtol=0, atol=0)
+    with pytest.raises(ValueError):
+        O.geometry(64.0, 512, qs, 3.0, 30.0, 12, window=("hann", "tukey"))
