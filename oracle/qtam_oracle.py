@@ -41,6 +41,18 @@ documented choice; the same list is kept in the design notes):
       of x onto F_tau.
   C9  a plane mask selects the planes whose rows are synthesised and whose
       windows enter P.
+  S1  streaming (the paper motivates hours-long signals, Sec. I, without
+      fixing a scheme): overlap-save with chunks of the plan's length N, hop H
+      and guard G = (N - H)/2 on each side; each chunk keeps its central
+      H M / N envelope columns.  H and G are multiples of N / gcd(N, M) so
+      that column and sample boundaries coincide.  A chunk starting a samples
+      after the stream origin has its envelopes multiplied by
+      exp(-2 pi i k_c a / N), so every chunk is demodulated against the same
+      time origin and the map is continuous across chunks (the inverse
+      multiplies by the conjugate).  The stream is preceded by
+      2G zeros; map column c is time c N/M - G, and the streaming inverse
+      (re-chunk the map the same way, keep each chunk's central H samples)
+      returns sample s at time s - 2G.
 
 Parity of every function here is pinned by the ``-m "not gpu"`` oracle tests.
 """
@@ -392,3 +404,66 @@ def plane_metrics(Y: np.ndarray):
     e = np.sum(np.abs(Y) ** 2, axis=(1, 2))
     pk = np.max(np.abs(Y) ** 2, axis=(1, 2))
     return e, pk, int(np.argmax(e)), int(np.argmax(pk))
+
+
+# ----------------------------------------------------------------------------
+# streaming (reading S1): overlap-save over a continuous signal
+# ----------------------------------------------------------------------------
+def stream_quantum(g: Geometry) -> int:
+    """Smallest sample count whose envelope column count is whole: N / gcd(N, M)."""
+    return g.N // math.gcd(g.N, g.M)
+
+
+def stream_layout(g: Geometry, hop: int):
+    """(G, Hn, Gm): guard samples, kept columns per chunk, guard columns."""
+    q = stream_quantum(g)
+    if hop <= 0 or hop > g.N or hop % q or (g.N - hop) % (2 * q):
+        raise ValueError("hop must be a positive multiple of the column quantum with (N - hop)/2 one too")
+    G = (g.N - hop) // 2
+    return G, hop * g.M // g.N, G * g.M // g.N
+
+
+def stream_phase(g: Geometry, a: int) -> np.ndarray:
+    """[P, K] factors exp(-2 pi i k_c a / N) that re-reference the envelopes of a
+    chunk starting at stream sample a to the stream origin (k_c a reduced mod N
+    in integers first)."""
+    m = np.mod(g.kc.astype(np.int64) * int(a), g.N)
+    return np.exp(-2j * np.pi * m / g.N)
+
+
+def stream_forward(g: Geometry, x: np.ndarray, hop: int) -> np.ndarray:
+    """Envelope map [P, K, J Hn] of a stream of J hops: chunk i is the N samples
+    starting at stream sample a = i hop - 2G (the stream is preceded by 2G
+    zeros); its envelopes, re-referenced by stream_phase(a), give columns
+    Gm .. Gm + Hn - 1 as map columns i Hn .. (i + 1) Hn - 1."""
+    G, Hn, Gm = stream_layout(g, hop)
+    x = np.asarray(x, dtype=np.float64)
+    if x.size % hop:
+        raise ValueError("the stream must be a whole number of hops")
+    J = x.size // hop
+    xp = np.concatenate([np.zeros(2 * G), x])
+    out = np.zeros((g.P, g.K, J * Hn), dtype=np.complex128)
+    for i in range(J):
+        Y = forward(g, xp[i * hop: i * hop + g.N]) * stream_phase(g, i * hop - 2 * G)[:, :, None]
+        out[:, :, i * Hn:(i + 1) * Hn] = Y[:, :, Gm:Gm + Hn]
+    return out
+
+
+def stream_inverse(g: Geometry, Ymap: np.ndarray, hop: int, planes=None, tau: float = 0.0) -> np.ndarray:
+    """Samples [J hop] from an envelope map of J Hn columns: chunk i takes the
+    map columns i Hn - 2 Gm .. i Hn - 2 Gm + M - 1 (zeros before the map),
+    which belong to the chunk starting at sample a = i hop - 3G of the forward
+    stream's time axis; it is taken back to its own origin (conjugate of
+    stream_phase(a)), inverted with Eq. qtam_canonical_inverse, and gives its
+    central hop samples G .. G + hop - 1."""
+    G, Hn, Gm = stream_layout(g, hop)
+    if Ymap.shape[2] % Hn:
+        raise ValueError("the map must be a whole number of chunks")
+    J = Ymap.shape[2] // Hn
+    Yp = np.concatenate([np.zeros((g.P, g.K, 2 * Gm), dtype=np.complex128), Ymap], axis=2)
+    out = np.zeros(J * hop)
+    for i in range(J):
+        Yi = Yp[:, :, i * Hn: i * Hn + g.M] * np.conj(stream_phase(g, i * hop - 3 * G))[:, :, None]
+        xh = inverse(g, Yi, planes=planes, tau=tau)
+        out[i * hop:(i + 1) * hop] = xh[G:G + hop]
+    return out

@@ -20,6 +20,8 @@ PIN_TESTS = [
     lambda gd: pins.test_bisquare_shape_and_moments(),
     lambda gd: pins.test_geometry_hand_derivations(gd),
     lambda gd: pins.test_grid_and_widths_follow_formulas(),
+    lambda gd: pins.test_stream_of_a_periodic_signal_tiles_the_circular_transform(),
+    lambda gd: pins.test_stream_layout_rules(),
 ]
 
 
@@ -66,6 +68,19 @@ def _acc_conj(g, Y, planes=None):
     return _orig_acc(g, np.conj(Y), planes)
 
 
+_orig_phase = O.stream_phase
+_orig_layout = O.stream_layout
+
+
+def _phase_wrong_sign(g, a):
+    return np.conj(_orig_phase(g, a))
+
+
+def _layout_crop_off_by_one(g, hop):
+    G, Hn, Gm = _orig_layout(g, hop)
+    return G, Hn, Gm + 1
+
+
 MUTANTS = {
     "ifft sign": ("forward_row", _fwd_wrong_sign),
     "dropped sqrt(M/N)": ("forward_row", _fwd_no_renorm),
@@ -74,6 +89,8 @@ MUTANTS = {
     "c_k squared": ("window_norm", _norm_sum_not_sqrt),
     "synthesis scale sqrt(M/N)": ("accumulate", _acc_wrong_scale),
     "synthesis of conj(Y)": ("accumulate", _acc_conj),
+    "stream phase conjugated": ("stream_phase", _phase_wrong_sign),
+    "stream crop one column late": ("stream_layout", _layout_crop_off_by_one),
 }
 
 

@@ -449,3 +449,53 @@ def test_composite_bank_planes_are_single_window_transforms():
     assert np.array_equal(gs.c, gb.c) and np.allclose(O.forward(gs, x), O.forward(gb, x), rtol=0, atol=0)
     with pytest.raises(ValueError):
         O.geometry(64.0, 512, qs, 3.0, 30.0, 12, window=("hann", "tukey"))
+
+
+# --------------------------------------------------------------------------- streaming (reading S1)
+def _stream_geom():
+    # N = 1024 at 256 Hz, M = 96 (gcd 32 -> quantum 32 samples = 3 columns)
+    return O.geometry(256.0, 1024, (6.0, 12.0), 2.0, 100.0, 20, n_out=96)
+
+
+def test_stream_layout_rules():
+    g = _stream_geom()
+    assert O.stream_quantum(g) == 32
+    assert O.stream_layout(g, 512) == (256, 48, 24)
+    assert O.stream_layout(g, 1024) == (0, 96, 0)
+    for bad in (0, 500, 2048, 544):        # not a quantum multiple / too long / odd guard count
+        with pytest.raises(ValueError):
+            O.stream_layout(g, bad)
+
+
+def test_stream_of_a_periodic_signal_tiles_the_circular_transform():
+    """A stream repeating one segment x0 is, away from the zero prefix, the
+    segment's circular transform tiled with the guard offset: map column c equals
+    Y0 column (c - Gm) mod M, and the streaming inverse returns the projection
+    of x0 delayed by 2G (shift invariance in whole columns, App. C)."""
+    g = _stream_geom()
+    hop = 512
+    G, Hn, Gm = O.stream_layout(g, hop)
+    x0 = _rand_x(g.N, 51)
+    reps = 6
+    x = np.tile(x0, reps)
+    Ymap = O.stream_forward(g, x, hop)
+    Y0 = O.forward(g, x0)
+    c0 = 2 * Hn                                   # chunks 0, 1 see the zero prefix
+    cols = np.arange(c0, Ymap.shape[2])
+    assert np.allclose(Ymap[:, :, cols], Y0[:, :, (cols - Gm) % g.M], rtol=0, atol=1e-12 * np.max(np.abs(Y0)))
+    xh = O.stream_inverse(g, Ymap, hop)
+    s0 = (2 + 2 * Gm // Hn + 2) * hop             # chunks whose envelopes come from clean map columns
+    s = np.arange(s0, xh.size)
+    xp0 = O.projection(g, x0)
+    assert np.allclose(xh[s], xp0[(s - 2 * G) % g.N], rtol=0, atol=1e-12 * np.max(np.abs(xp0)))
+
+
+def test_stream_without_guard_is_chunkwise():
+    g = _stream_geom()
+    x = _rand_x(3 * g.N, 52)
+    Ymap = O.stream_forward(g, x, g.N)
+    for i in range(3):
+        Yi = O.forward(g, x[i * g.N:(i + 1) * g.N])
+        assert np.array_equal(Ymap[:, :, i * g.M:(i + 1) * g.M], Yi)
+        assert np.allclose(O.stream_inverse(g, Ymap, g.N)[i * g.N:(i + 1) * g.N], O.inverse(g, Yi), rtol=0,
+                           atol=1e-13 * np.max(np.abs(x)))
