@@ -259,6 +259,65 @@ QTAM_API qtam_status qtam_inverse_batched(const qtam_group* groups, int32_t n_gr
  * array's address; make it before any stream capture. */
 QTAM_API qtam_status qtam_forward_noalloc(qtam_plan_t plan, const void* x, int64_t batch, void* y, void* stream);
 
+/* ---- Streaming analysis of a continuous signal (overlap-save) ----------
+ * The paper motivates hours-long signals (Sec. I) without fixing a scheme;
+ * this is overlap-save over the plan's segment length N.  Chunks of N
+ * samples advance by `hop` samples; the guard G = (N - hop)/2 on each side
+ * absorbs the circular wrap of each chunk's transform and only the central
+ * Hn = hop*M/N envelope columns of a chunk are kept.  hop and G must be
+ * multiples of the column quantum N / gcd(N, M), where column and sample
+ * boundaries coincide.  A chunk starting a samples after the stream origin
+ * has its envelope rows multiplied by exp(-2 pi i k_c a / N), so every chunk
+ * is demodulated against the same time origin and the map is continuous
+ * across chunks.  The stream starts after 2G zero samples: map column c is
+ * time c*N/M - G (forward delay G), and the streaming inverse returns sample
+ * s at time s - 2G (a further G).
+ *
+ * The stream object keeps the last 2G input samples and the last 2G*M/N map
+ * columns of every row as history, plus scratch for `max_chunks` chunks per
+ * internal step (pushes longer than that run in several steps).  It owns
+ * its device memory (allocated in qtam_stream_create, freed by
+ * qtam_stream_destroy) and references the plan, which must outlive it.  A
+ * stream's calls must be ordered on the GPU (one CUDA stream, or events). */
+typedef struct qtam_stream_s* qtam_stream_t;
+
+typedef struct {
+  int64_t hop;         /* samples per chunk step */
+  int64_t guard;       /* G = (N - hop) / 2 */
+  int64_t quantum;     /* N / gcd(N, M) */
+  int32_t hop_cols;    /* Hn = hop * M / N map columns per chunk */
+  int32_t guard_cols;  /* G * M / N */
+  int64_t max_chunks;  /* chunks per internal step */
+  int64_t samples_in;  /* samples consumed by qtam_stream_forward since create / reset */
+  int64_t columns_in;  /* map columns consumed by qtam_stream_inverse since create / reset */
+  int64_t device_bytes;
+} qtam_stream_info_t;
+
+/* Create a stream over a device plan.  hop = 0 selects N/2 rounded down to
+ * the quantum grid.  max_chunks >= 1.  Errors: QTAM_ERR_INVALID_ARG (hop or
+ * guard off the quantum grid, hop > N), QTAM_ERR_NO_DEVICE (host-only plan),
+ * QTAM_ERR_OUT_OF_MEMORY.  Synchronous. */
+QTAM_API qtam_status qtam_stream_create(qtam_plan_t plan, int64_t hop, int64_t max_chunks, qtam_stream_t* out);
+QTAM_API qtam_status qtam_stream_info(qtam_stream_t s, qtam_stream_info_t* out);
+
+/* Push n samples (device, the plan's real dtype; n a multiple of hop) and
+ * receive their (n/hop)*Hn map columns: y is a device array [P][K][n/hop*Hn]
+ * of the plan's envelope dtype (interleaved complex), each row contiguous.
+ * n = 0 is a no-op.  Enqueued on `stream`. */
+QTAM_API qtam_status qtam_stream_forward(qtam_stream_t s, const void* x, int64_t n, void* y, void* stream);
+
+/* Push n_cols map columns (device [P][K][n_cols], n_cols a multiple of Hn;
+ * any values, e.g. a masked map) and receive (n_cols/Hn)*hop samples of the
+ * canonical-dual reconstruction of the planes in plane_mask (0 = all). */
+QTAM_API qtam_status qtam_stream_inverse(qtam_stream_t s, const void* y, int64_t n_cols, uint64_t plane_mask,
+                                         void* x, void* stream);
+
+/* Zero both histories and positions (enqueued on `stream`). */
+QTAM_API qtam_status qtam_stream_reset(qtam_stream_t s, void* stream);
+
+/* Free the stream's device memory (synchronises the device first).  NULL is a no-op. */
+QTAM_API qtam_status qtam_stream_destroy(qtam_stream_t s);
+
 /* Release the plan's device tables and the plan.  NULL is a no-op. */
 QTAM_API qtam_status qtam_destroy(qtam_plan_t plan);
 

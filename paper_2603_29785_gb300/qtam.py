@@ -50,6 +50,14 @@ class qtam_plan_desc(ctypes.Structure):
     ]
 
 
+class qtam_stream_info_t(ctypes.Structure):
+    _fields_ = [
+        ("hop", ctypes.c_int64), ("guard", ctypes.c_int64), ("quantum", ctypes.c_int64),
+        ("hop_cols", ctypes.c_int32), ("guard_cols", ctypes.c_int32), ("max_chunks", ctypes.c_int64),
+        ("samples_in", ctypes.c_int64), ("columns_in", ctypes.c_int64), ("device_bytes", ctypes.c_int64),
+    ]
+
+
 class qtam_group(ctypes.Structure):
     _fields_ = [("plan", ctypes.c_void_p), ("input", ctypes.c_void_p), ("output", ctypes.c_void_p),
                 ("batch", ctypes.c_int64)]
@@ -96,6 +104,12 @@ SIGNATURES = {
     "qtam_batched_workspace_size": (ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_SZ)]),
     "qtam_forward_batched": (ctypes.c_int, [_P, ctypes.c_int32, _P, _SZ, _P]),
     "qtam_inverse_batched": (ctypes.c_int, [_P, ctypes.c_int32, _U64, _P, _SZ, _P]),
+    "qtam_stream_create": (ctypes.c_int, [_P, _I64, _I64, ctypes.POINTER(_P)]),
+    "qtam_stream_info": (ctypes.c_int, [_P, ctypes.POINTER(qtam_stream_info_t)]),
+    "qtam_stream_forward": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
+    "qtam_stream_inverse": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P]),
+    "qtam_stream_reset": (ctypes.c_int, [_P, _P]),
+    "qtam_stream_destroy": (ctypes.c_int, [_P]),
     "qtam_destroy": (ctypes.c_int, [_P]),
     "qtam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qtam_last_error": (ctypes.c_char_p, []),
@@ -324,6 +338,35 @@ def qtam_destroy(plan):
         lib().qtam_destroy(plan)
 
 
+def qtam_stream_create(plan, hop: int = 0, max_chunks: int = 8) -> int:
+    h = _P()
+    _check(lib().qtam_stream_create(plan, int(hop), int(max_chunks), ctypes.byref(h)))
+    return h.value
+
+
+def qtam_stream_info(s) -> dict:
+    o = qtam_stream_info_t()
+    _check(lib().qtam_stream_info(s, ctypes.byref(o)))
+    return {k: getattr(o, k) for k, _ in qtam_stream_info_t._fields_}
+
+
+def qtam_stream_forward(s, x, n, y, stream=None):
+    _check(lib().qtam_stream_forward(s, _ptr(x), int(n), _ptr(y), _stream(stream)))
+
+
+def qtam_stream_inverse(s, y, n_cols, plane_mask, x, stream=None):
+    _check(lib().qtam_stream_inverse(s, _ptr(y), int(n_cols), int(plane_mask), _ptr(x), _stream(stream)))
+
+
+def qtam_stream_reset(s, stream=None):
+    _check(lib().qtam_stream_reset(s, _stream(stream)))
+
+
+def qtam_stream_destroy(s):
+    if s:
+        lib().qtam_stream_destroy(s)
+
+
 def qtam_status_string(status: int) -> str:
     return lib().qtam_status_string(int(status)).decode()
 
@@ -510,6 +553,71 @@ class Plan:
         ws, wsb = self.workspace(B)
         qtam_stage_synthesize(self.handle, A, B, plane_mask, x, ws, wsb, stream)
         return x
+
+
+class Stream:
+    """Overlap-save streaming over a continuous signal with a device plan.
+
+    Stream(plan, hop=0, max_chunks=8): hop = 0 picks N/2 on the column
+    quantum grid.  forward(x) takes a 1-D device tensor of a multiple of hop
+    samples and returns the new map columns [P, K, n/hop*Hn]; inverse(y)
+    takes map columns and returns samples.  Map column c of the whole stream
+    is time c*N/M - guard; inverse sample s is time s - 2*guard.
+    """
+
+    def __init__(self, plan: Plan, hop: int = 0, max_chunks: int = 8):
+        self.plan = plan
+        self.handle = qtam_stream_create(plan.handle, hop, max_chunks)
+        self.info = qtam_stream_info(self.handle)
+        self.hop = self.info["hop"]
+        self.guard = self.info["guard"]
+        self.hop_cols = self.info["hop_cols"]
+
+    def __del__(self):
+        try:
+            qtam_stream_destroy(self.handle)
+        except Exception:
+            pass
+
+    def _map_tensor(self, cols):
+        import torch
+        p = self.plan
+        dev = f"cuda:{p.device}"
+        shp = (p.P, p.K, cols)
+        if p.envelope == "f32":
+            return torch.empty(shp, dtype=torch.complex64, device=dev)
+        if p.envelope == "f64":
+            return torch.empty(shp, dtype=torch.complex128, device=dev)
+        dt = torch.bfloat16 if p.envelope == "bf16" else torch.float16
+        return torch.empty(shp + (2,), dtype=dt, device=dev)
+
+    def forward(self, x, stream=None):
+        p = self.plan
+        _require(x, (None,), (p.real_dtype(),), p.device, "x")
+        n = int(x.shape[0])
+        if n % self.hop:
+            raise ValueError(f"push a multiple of hop = {self.hop} samples; got {n}")
+        y = self._map_tensor(n // self.hop * self.hop_cols)
+        qtam_stream_forward(self.handle, x, n, y, stream)
+        return y
+
+    def inverse(self, y, plane_mask: int = 0, stream=None):
+        import torch
+        p = self.plan
+        if p.envelope in ("bf16", "f16"):
+            dt = torch.bfloat16 if p.envelope == "bf16" else torch.float16
+            _require(y, (p.P, p.K, None, 2), (dt,), p.device, "y")
+        else:
+            _require(y, (p.P, p.K, None), (p.complex_dtype(),), p.device, "y")
+        cols = int(y.shape[2])
+        if cols % self.hop_cols:
+            raise ValueError(f"push a multiple of {self.hop_cols} map columns; got {cols}")
+        x = torch.empty((cols // self.hop_cols * self.hop,), dtype=p.real_dtype(), device=y.device)
+        qtam_stream_inverse(self.handle, y, cols, plane_mask, x, stream)
+        return x
+
+    def reset(self, stream=None):
+        qtam_stream_reset(self.handle, stream)
 
 
 def header_symbols(header_path: str | None = None) -> list[str]:

@@ -141,6 +141,17 @@ def test_window_argument_errors_and_variants():
         qtam.Plan(*base[:2], (8, 16), *base[3:], window=("hann",), device=-1)
 
 
+def test_stream_argument_errors():
+    """Streaming (overlap-save) layout rules are checked before anything is
+    allocated: hop and guard on the column quantum N / gcd(N, M)."""
+    p = qtam.Plan(256.0, 1024, (6.0, 12.0), 2.0, 100.0, 20, n_out=96, device=-1)   # quantum 32
+    for hop in (500, 2048, 544, -32):
+        assert _err(lambda: qtam.qtam_stream_create(p.handle, hop, 4)) == 1
+    assert _err(lambda: qtam.qtam_stream_create(p.handle, 512, 0)) == 1
+    assert _err(lambda: qtam.qtam_stream_create(p.handle, 512, 4)) == 8        # host-only plan
+    assert _err(lambda: qtam.qtam_stream_create(p.handle, 0, 4)) == 8          # default hop is valid
+
+
 def test_f64_defaults():
     p = qtam.Plan(4096, 16384, (8,), 20, 1024, 64, compute="f64", device=-1)
     assert p.info["p_floor_rel"] == 0.0 and p.info["envelope_bytes_per_segment"] == 64 * 250 * 16
