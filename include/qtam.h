@@ -318,6 +318,22 @@ QTAM_API qtam_status qtam_stream_reset(qtam_stream_t s, void* stream);
 /* Free the stream's device memory (synchronises the device first).  NULL is a no-op. */
 QTAM_API qtam_status qtam_stream_destroy(qtam_stream_t s);
 
+/* ---- Tensor-core building block check ------------------------------------
+ * One 128 x N x K BF16 matrix product on the fifth-generation tensor cores
+ * (tcgen05: shared-memory operands, FP32 accumulator in tensor memory), the
+ * building block of the tensor-core short DFT: D[128][N] = A[128][K] *
+ * B[N][K]^T with A, B row-major BF16 (raw 16-bit patterns) and D row-major
+ * FP32, all device buffers owned by the caller; flags bit 0 negates A, bit 1
+ * negates B.  N, K multiples of 16 in [16, 256]; A, B 16-byte aligned.
+ * Enqueued on `stream`; a tensor-core wait that runs out (about 1 s) is
+ * counted and reported by qtam_tc_status. */
+QTAM_API qtam_status qtam_tc_gemm_check(const void* A, const void* B, float* D, int32_t N, int32_t K, int32_t flags,
+                                        void* stream);
+/* Number of bounded tensor-core waits that ran out since the library was
+ * loaded on the current device (0 when every tensor-core kernel completed).
+ * Synchronous. */
+QTAM_API qtam_status qtam_tc_status(int32_t* timeouts);
+
 /* Release the plan's device tables and the plan.  NULL is a no-op. */
 QTAM_API qtam_status qtam_destroy(qtam_plan_t plan);
 

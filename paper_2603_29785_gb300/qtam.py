@@ -110,6 +110,8 @@ SIGNATURES = {
     "qtam_stream_inverse": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P]),
     "qtam_stream_reset": (ctypes.c_int, [_P, _P]),
     "qtam_stream_destroy": (ctypes.c_int, [_P]),
+    "qtam_tc_gemm_check": (ctypes.c_int, [_P, _P, _P, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
+    "qtam_tc_status": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int32)]),
     "qtam_destroy": (ctypes.c_int, [_P]),
     "qtam_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "qtam_last_error": (ctypes.c_char_p, []),
@@ -365,6 +367,16 @@ def qtam_stream_reset(s, stream=None):
 def qtam_stream_destroy(s):
     if s:
         lib().qtam_stream_destroy(s)
+
+
+def qtam_tc_gemm_check(A, B, D, N, K, flags=0, stream=None):
+    _check(lib().qtam_tc_gemm_check(_ptr(A), _ptr(B), _ptr(D), int(N), int(K), int(flags), _stream(stream)))
+
+
+def qtam_tc_status() -> int:
+    v = ctypes.c_int32()
+    _check(lib().qtam_tc_status(ctypes.byref(v)))
+    return v.value
 
 
 def qtam_status_string(status: int) -> str:
