@@ -81,6 +81,7 @@ enum { QTAM_WIN_BISQUARE = 0, QTAM_WIN_HANN = 1, QTAM_WIN_KAISER = 2, QTAM_WIN_T
  * NONE = 1. */
 enum { QTAM_NORM_L2 = 0, QTAM_NORM_PAPER = 1, QTAM_NORM_NONE = 2 };
 enum { QTAM_DTYPE_F32 = 0, QTAM_DTYPE_F64 = 1, QTAM_DTYPE_BF16 = 2, QTAM_DTYPE_F16 = 3 };
+enum { QTAM_SHORT_DFT_CUDA = 0, QTAM_SHORT_DFT_TENSOR = 1 };
 
 typedef struct {
   double sample_rate;     /* f_s in Hz, > 0 */
@@ -105,6 +106,14 @@ typedef struct {
    * only; the caller keeps ownership.  Planes may repeat a Q value. */
   const int32_t* plane_window;
   const double* plane_window_param;
+  /* short DFT engine of the envelope stage: QTAM_SHORT_DFT_CUDA (default:
+   * FP32 mixed-radix FFTs on the CUDA cores) or QTAM_SHORT_DFT_TENSOR (the
+   * length-8192 DFT as a 64 x 128 four-step whose two DFT stages are BF16
+   * matrix products on the tensor cores with FP32 accumulation and an FP32
+   * twiddle between them; needs n_out = 8192 and F32 compute, else
+   * QTAM_ERR_UNSUPPORTED_SIZE).  Its envelopes carry BF16 operand rounding
+   * (relative error ~1e-3); the inverse stays on the CUDA cores. */
+  int32_t short_dft;
 } qtam_plan_desc;
 
 typedef struct {
@@ -124,7 +133,8 @@ typedef struct {
   double kappa;                   /* max over kept bins of max_k W_k / P (all planes) */
   int64_t kept_bins;              /* |F_tau| for all planes */
   int64_t device_bytes;           /* bytes of resident plan tables on the device */
-  int32_t row_variant;            /* row-kernel variant in use (-1: runtime engine) */
+  int32_t row_variant;            /* row-kernel variant in use (-1: runtime engine; -2: tensor-core
+                                     forward with the runtime engine for the inverse) */
 } qtam_plan_info_t;
 
 /* Fill *d with defaults: bisquare, L2 norm, q_width sqrt(11), automatic clamp

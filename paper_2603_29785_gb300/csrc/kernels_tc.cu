@@ -2,7 +2,9 @@
 // descriptors, tensor-memory allocation, MMA, commit and loads on their own,
 // and the tensor-core short DFT of the row kernels.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
+#include <algorithm>
 #include <string>
 
 #include "../../include/qtam.h"
@@ -75,7 +77,268 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0) tc::tmem_dealloc(tbase, ncols);
 }
 
+// ---- tensor-core short DFT of the row kernels (M = 8192 = 64 x 128) ----------
+//
+// Forward rows (steps a2-a4), two rows per CTA iteration.  With j = 128 j1 +
+// j2 and n = n1 + 64 n2 the length-8192 inverse DFT of the windowed band Z
+// factors into (four-step):
+//   D[n1][j2]  = sum_j1 e^{+2 pi i j1 n1/64} Z[128 j1 + j2]     GEMM A (tensor cores)
+//   D'[n1][j2] = D[n1][j2] e^{+2 pi i j2 n1/8192}               twiddle (FP32, CUDA cores)
+//   Y[n1+64n2] = sum_j2 D'[n1][j2] e^{+2 pi i j2 n2/128}        GEMM B (tensor cores)
+// Complex products are real GEMMs on (re, im) blocks with BF16 operands and
+// FP32 accumulation in tensor memory:
+//   GEMM A: M = 128 rows (2 n1 + re/im), K = 128 (j1 of Re Z, j1 of Im Z),
+//           N = 256 columns (j2 of row 0, j2 of row 1); A = the DFT-64 block
+//           matrix (constant), B = Z written by the band gather.
+//   GEMM B: M = 128 rows (64 r + n1), K = 128 per part, N = 128 + 128
+//           (Re Y, Im Y): Re Y = Re D' Gr - Im D' Gi, Im Y = Re D' Gi + Im D' Gr
+//           with Gr, Gi the cosine / sine DFT-128 matrices (constant, the
+//           minus sign through the MMA's negate-A bit).
+// Shared memory: DFT-64 block 32 KB, Gr 32 KB, Gi 32 KB, one 64 KB operand
+// buffer used first for Z (GEMM A's B) and then for D' (GEMM B's A).
+// Tensor memory: 512 columns, D in 0..255, Y in 256..511.
+constexpr int kTcM = 8192;
+constexpr int kTcThreads = 256;
+constexpr size_t kTcSmem = 5 * 32768 + 32768;   // constants (96 KB) + operand buffer (64 KB) + 32 KB slack
+
+template <int E> struct TcEnv;
+template <> struct TcEnv<ENV_F32> {
+  using S = float2;
+  __device__ static S to(float a, float b) { return make_float2(a, b); }
+};
+template <> struct TcEnv<ENV_BF16> {
+  using S = __nv_bfloat162;
+  __device__ static S to(float a, float b) { return __floats2bfloat162_rn(a, b); }
+};
+template <> struct TcEnv<ENV_F16> {
+  using S = __half2;
+  __device__ static S to(float a, float b) { return __floats2half2_rn(a, b); }
+};
+
+__device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+template <int E>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_rows_forward_tc(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
+                      typename TcEnv<E>::S* __restrict__ y, int64_t n_units, const uint4* __restrict__ tabA,
+                      const uint4* __restrict__ tabG, const float2* __restrict__ tw, const float* __restrict__ wtab) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  unsigned char* sA = sm;                 // DFT-64 block, [128][128] K-major
+  unsigned char* sGr = sm + 32768;        // [128 n2][128 j2]
+  unsigned char* sGi = sm + 65536;
+  unsigned char* sD = sm + 98304;         // Z as [256 c][128 k], then D' as [128 m][256 k]
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < 2048; i += kTcThreads) reinterpret_cast<uint4*>(sA)[i] = tabA[i];
+  for (int i = tid; i < 4096; i += kTcThreads) reinterpret_cast<uint4*>(sGr)[i] = tabG[i];
+  if (warp == 0) {
+    tc::tmem_alloc(&tslot, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbar, 1);
+    abort_flag = 0;
+  }
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tslot;
+  const uint32_t aA = tc::smem_addr(sA), aGr = tc::smem_addr(sGr), aGi = tc::smem_addr(sGi), aD = tc::smem_addr(sD);
+  const int64_t nhalf = Nr - 1;
+  const int64_t n_pairs = (n_units + 1) >> 1;
+  uint32_t phase = 0;
+  bool pending = false;
+
+  for (int64_t pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
+    // ---- 1. band gather + window -> Z (GEMM A's B operand) ----
+    {
+      const int r = tid >> 7, j2 = tid & 127;
+      const int64_t u = 2 * pr + r;
+      const bool valid = u < n_units;
+      const int64_t seg = valid ? u / n_rows : 0;
+      const int row = valid ? (int)(u - seg * n_rows) : 0;
+      const RowDev<float> rd = rows[row];
+      const int dhi = (int)min((int64_t)rd.h, nhalf - rd.kc);
+      const int dlo = (int)max((int64_t)-rd.h, (int64_t)-rd.kc);
+      const int mlo = kTcM + dlo;
+      const float2* Xs = X + seg * Nr + rd.kc;
+      const bool tab = wtab != nullptr && rd.woff >= 0;
+      const unsigned c = 128u * r + j2;
+#pragma unroll 2
+      for (int o = 0; o < 8; ++o) {
+        float re[8], im[8];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int j = 128 * (8 * o + e) + j2;
+          const bool lo = j <= dhi, hi = j >= mlo;
+          const int d = lo ? j : j - kTcM;
+          float2 v = make_float2(0.f, 0.f);
+          if (valid && (lo || hi)) v = Xs[d];
+          const int a = min(d < 0 ? -d : d, rd.h);
+          float w;
+          if (tab) {
+            w = rd.c_fwd * wtab[rd.woff + a];
+          } else {
+            const float uu = (float)((rd.h - a) * (rd.h + a)) * rd.kw_fwd;
+            w = uu * uu;
+          }
+          re[e] = v.x * w;
+          im[e] = v.y * w;
+        }
+        const uint4 pr4 = make_uint4(pack_bf16(re[0], re[1]), pack_bf16(re[2], re[3]), pack_bf16(re[4], re[5]),
+                                     pack_bf16(re[6], re[7]));
+        const uint4 pi4 = make_uint4(pack_bf16(im[0], im[1]), pack_bf16(im[2], im[3]), pack_bf16(im[4], im[5]),
+                                     pack_bf16(im[6], im[7]));
+        *reinterpret_cast<uint4*>(sD + tc::cm_offset(c, 8 * o, 128)) = pr4;
+        *reinterpret_cast<uint4*>(sD + tc::cm_offset(c, 64 + 8 * o, 128)) = pi4;
+      }
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- 2. GEMM A: D[tmem 0..255] = DFT64 * Z ----
+    if (tid == 0) {
+      const uint32_t idesc = tc::make_idesc_bf16(128, 256);
+#pragma unroll
+      for (int s = 0; s < 8; ++s)
+        tc::mma_bf16(tbase, tc::make_sdesc(aA + 256u * s, 128u, 2048u), tc::make_sdesc(aD + 256u * s, 128u, 2048u),
+                     idesc, s > 0);
+      tc::mma_commit(&mbar);
+    }
+    pending = true;
+    if (!tc::mbar_wait_bounded(&mbar, phase, tc::kWaitCycles)) abort_flag = 1;
+    tc::fence_after_sync();
+    __syncthreads();
+    if (abort_flag) break;
+    phase ^= 1u;
+    pending = false;
+    // ---- 3. twiddle D -> D' (GEMM B's A operand, [128 m = 64 r + n1][256 k = Re j2 | Im j2]) ----
+    {
+      const int q4 = warp & 3, rh = warp >> 2;
+      const int n1 = 16 * q4 + (lane >> 1), part = lane & 1;
+      const unsigned m = 64u * rh + n1;
+      const float2* twr = tw + n1 * 128;
+#pragma unroll 1
+      for (int q = 0; q < 8; ++q) {
+        float v[16];
+        tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(128 * rh + 16 * q), v);
+        float o[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const float p = __shfl_xor_sync(0xffffffffu, v[e], 1);
+          const float re = part ? p : v[e], im = part ? v[e] : p;
+          const float2 t = twr[16 * q + e];
+          o[e] = part ? fmaf(re, t.y, im * t.x) : fmaf(re, t.x, -im * t.y);
+        }
+        const unsigned k0 = 128u * part + 16u * q;
+        *reinterpret_cast<uint4*>(sD + tc::cm_offset(m, k0, 256)) =
+            make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]), pack_bf16(o[4], o[5]), pack_bf16(o[6], o[7]));
+        *reinterpret_cast<uint4*>(sD + tc::cm_offset(m, k0 + 8, 256)) = make_uint4(
+            pack_bf16(o[8], o[9]), pack_bf16(o[10], o[11]), pack_bf16(o[12], o[13]), pack_bf16(o[14], o[15]));
+      }
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- 4. GEMM B: Re Y [tmem 256..383], Im Y [384..511] ----
+    if (tid == 0) {
+      const uint32_t id = tc::make_idesc_bf16(128, 128), idn = tc::make_idesc_bf16(128, 128, true);
+      const uint32_t tRe = tbase + 256u, tIm = tbase + 384u;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {   // Re D' * Gr, Re D' * Gi
+        const uint64_t a = tc::make_sdesc(aD + 256u * s, 128u, 4096u);
+        tc::mma_bf16(tRe, a, tc::make_sdesc(aGr + 256u * s, 128u, 2048u), id, s > 0);
+        tc::mma_bf16(tIm, a, tc::make_sdesc(aGi + 256u * s, 128u, 2048u), id, s > 0);
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {   // - Im D' * Gi, + Im D' * Gr
+        const uint64_t a = tc::make_sdesc(aD + 256u * (8 + s), 128u, 4096u);
+        tc::mma_bf16(tRe, a, tc::make_sdesc(aGi + 256u * s, 128u, 2048u), idn, 1u);
+        tc::mma_bf16(tIm, a, tc::make_sdesc(aGr + 256u * s, 128u, 2048u), id, 1u);
+      }
+      tc::mma_commit(&mbar);
+    }
+    pending = true;
+    if (!tc::mbar_wait_bounded(&mbar, phase, tc::kWaitCycles)) abort_flag = 1;
+    tc::fence_after_sync();
+    __syncthreads();
+    if (abort_flag) break;
+    phase ^= 1u;
+    pending = false;
+    // ---- 5. envelopes out: y[u][n1 + 64 n2] ----
+    {
+      const int q4 = warp & 3, half = warp >> 2;
+      const int r = q4 >> 1, n1 = 32 * (q4 & 1) + lane;
+      const int64_t u = 2 * pr + r;
+      if (u < n_units) {
+        typename TcEnv<E>::S* yu = y + u * kTcM + n1;
+#pragma unroll 1
+        for (int q = 0; q < 4; ++q) {
+          const int n20 = 64 * half + 16 * q;
+          float vr[16], vi[16];
+          tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + 256u + (uint32_t)n20, vr);
+          tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + 384u + (uint32_t)n20, vi);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) __stcs(yu + 64 * (n20 + e), TcEnv<E>::to(vr[e], vi[e]));
+        }
+      }   // r is uniform per warp, so the warp-collective loads are skipped by whole warps only
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+  }
+  if (abort_flag) {
+    if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
+    if (pending) tc::mbar_wait_bounded(&mbar, phase, tc::kWaitCycles);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
 }  // namespace
+
+bool tc_forward_supported(int M) { return M == kTcM; }
+
+cudaError_t launch_rows_forward_tc(const RowCfg& c, const RowDev<float>* rows, int n_rows, int64_t Nr,
+                                   const float2* X, void* y, int env, int64_t B, cudaStream_t st, const float* wtab) {
+  const int64_t units = B * n_rows;
+  if (units == 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t pairs = (units + 1) / 2;
+  const unsigned grid = (unsigned)std::min<int64_t>(pairs, (int64_t)std::max(sms, 1));
+  const uint4* A = static_cast<const uint4*>(c.tcA);
+  const uint4* G = static_cast<const uint4*>(c.tcG);
+  const float2* tw = static_cast<const float2*>(c.tcTw);
+  cudaError_t e;
+  switch (env) {
+    case ENV_BF16:
+      if ((e = allow_smem((const void*)k_rows_forward_tc<ENV_BF16>, kTcSmem)) != cudaSuccess) return e;
+      k_rows_forward_tc<ENV_BF16><<<grid, kTcThreads, kTcSmem, st>>>(
+          rows, n_rows, Nr, X, static_cast<__nv_bfloat162*>(y), units, A, G, tw, wtab);
+      break;
+    case ENV_F16:
+      if ((e = allow_smem((const void*)k_rows_forward_tc<ENV_F16>, kTcSmem)) != cudaSuccess) return e;
+      k_rows_forward_tc<ENV_F16><<<grid, kTcThreads, kTcSmem, st>>>(rows, n_rows, Nr, X, static_cast<__half2*>(y),
+                                                                    units, A, G, tw, wtab);
+      break;
+    default:
+      if ((e = allow_smem((const void*)k_rows_forward_tc<ENV_F32>, kTcSmem)) != cudaSuccess) return e;
+      k_rows_forward_tc<ENV_F32><<<grid, kTcThreads, kTcSmem, st>>>(rows, n_rows, Nr, X, static_cast<float2*>(y),
+                                                                    units, A, G, tw, wtab);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace qtam
 
 extern "C" {

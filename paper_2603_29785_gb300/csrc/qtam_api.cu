@@ -30,6 +30,7 @@
 
 #include "../../include/qtam.h"
 #include "qtam_internal.h"
+#include "tc_sm100.cuh"
 
 using namespace qtam;
 
@@ -172,6 +173,7 @@ struct qtam_plan_s {
   std::vector<double> window_param; // per plane
   int compute = QTAM_DTYPE_F32;
   int env = QTAM_DTYPE_F32;
+  int short_dft = QTAM_SHORT_DFT_CUDA;
   double tau = 0;
   // geometry
   int P = 0;
@@ -194,6 +196,9 @@ struct qtam_plan_s {
   void* d_twN = nullptr;
   void* d_tw4 = nullptr;
   void* d_wtab = nullptr;   // W'(0..h) per distinct half-width, non-bisquare windows only
+  void* d_tcA = nullptr;    // tensor-core short DFT operands and twiddles (short_dft = TENSOR)
+  void* d_tcG = nullptr;
+  void* d_tcTw = nullptr;
   size_t device_bytes = 0;
   std::map<int, void*> variant_tw;   // stage twiddle tables per row-kernel variant
   void* d_stw_col = nullptr;
@@ -360,6 +365,54 @@ qtam_status upload_stage_table(const int* r, int nst, void** dst, size_t& total)
   return upload(dst, f.data(), f.size() * sizeof(float), total);
 }
 
+// round to the nearest BF16, ties to even (finite inputs)
+uint16_t to_bf16(double x) {
+  const float f = (float)x;
+  uint32_t b;
+  std::memcpy(&b, &f, 4);
+  b += 0x7FFFu + ((b >> 16) & 1u);
+  return (uint16_t)(b >> 16);
+}
+
+// Operands of the tensor-core four-step (M = 64 x 128), FP64-evaluated and
+// rounded once, in the K-major core-matrix layout of the MMA operands:
+//  A: DFT-64 block matrix, row 2 n1 + {re, im}, column j1 (times Re Z) or
+//     64 + j1 (times Im Z): [cos, -sin; sin, cos] of 2 pi j1 n1 / 64;
+//  G: cosine then sine DFT-128 matrices [n2][j2] of 2 pi j2 n2 / 128;
+//  twiddles e^{+2 pi i j2 n1 / 8192}, [n1][j2] complex FP32.
+qtam_status upload_tc_tables(qtam_plan_s* pl, size_t& tot) {
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<uint16_t> A(128 * 128), G(2 * 128 * 128);
+  for (int m = 0; m < 128; ++m)
+    for (int k = 0; k < 128; ++k) {
+      const int n1 = m >> 1, part = m & 1, j1 = k & 63, comp = k >> 6;
+      const double th = two_pi * (double)((j1 * n1) % 64) / 64.0;
+      const double v = part == 0 ? (comp == 0 ? std::cos(th) : -std::sin(th)) : (comp == 0 ? std::sin(th) : std::cos(th));
+      A[qtam::tc::cm_offset(m, k, 128) / 2] = to_bf16(v);
+    }
+  for (int n2 = 0; n2 < 128; ++n2)
+    for (int j2 = 0; j2 < 128; ++j2) {
+      const double th = two_pi * (double)((j2 * n2) % 128) / 128.0;
+      G[qtam::tc::cm_offset(n2, j2, 128) / 2] = to_bf16(std::cos(th));
+      G[128 * 128 + qtam::tc::cm_offset(n2, j2, 128) / 2] = to_bf16(std::sin(th));
+    }
+  std::vector<float> tw(2 * 64 * 128);
+  for (int n1 = 0; n1 < 64; ++n1)
+    for (int j2 = 0; j2 < 128; ++j2) {
+      const double th = two_pi * (double)((j2 * n1) % 8192) / 8192.0;
+      tw[2 * (n1 * 128 + j2)] = (float)std::cos(th);
+      tw[2 * (n1 * 128 + j2) + 1] = (float)std::sin(th);
+    }
+  qtam_status s;
+  if ((s = upload(&pl->d_tcA, A.data(), A.size() * 2, tot)) != QTAM_OK) return s;
+  if ((s = upload(&pl->d_tcG, G.data(), G.size() * 2, tot)) != QTAM_OK) return s;
+  if ((s = upload(&pl->d_tcTw, tw.data(), tw.size() * sizeof(float), tot)) != QTAM_OK) return s;
+  pl->rc.tcA = pl->d_tcA;
+  pl->rc.tcG = pl->d_tcG;
+  pl->rc.tcTw = pl->d_tcTw;
+  return QTAM_OK;
+}
+
 template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
   std::vector<T> tw;
   size_t tot = 0;
@@ -416,6 +469,7 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
     if ((s = upload(&pl->d_wtab, tab.data(), tab.size() * sizeof(T), tot)) != QTAM_OK) return s;
   }
   if ((s = upload(&pl->d_rows, rows.data(), rows.size() * sizeof(RowDev<T>), tot)) != QTAM_OK) return s;
+  if (pl->rc.tensor && (s = upload_tc_tables(pl, tot)) != QTAM_OK) return s;
   if (sizeof(T) == 4) {
     for (int v = 0; v < row_variant_count(); ++v) {
       const RowVariant* rv = row_variant(v);
@@ -451,6 +505,9 @@ void free_plan(qtam_plan_s* pl) {
     cudaFree(pl->d_twN);
     cudaFree(pl->d_tw4);
     cudaFree(pl->d_wtab);
+    cudaFree(pl->d_tcA);
+    cudaFree(pl->d_tcG);
+    cudaFree(pl->d_tcTw);
     cudaFree(pl->d_stw_col);
     cudaFree(pl->d_stw_row);
     for (auto& kv : pl->variant_tw) cudaFree(kv.second);
@@ -505,6 +562,15 @@ qtam_status run_spectrum(qtam_plan_s* pl, const void* x, int64_t B, void* X, voi
 }
 
 template <typename T> qtam_status run_envelopes(qtam_plan_s* pl, const void* X, int64_t B, void* y, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (pl->rc.tensor) {
+      cudaError_t e = launch_rows_forward_tc(pl->rc, static_cast<const RowDev<float>*>(pl->d_rows), pl->P * pl->K,
+                                             pl->Nr, static_cast<const float2*>(X), y, pl->env, B, st,
+                                             static_cast<const float*>(pl->d_wtab));
+      if (e != cudaSuccess) return fail_cuda(e, "tensor-core envelopes");
+      return QTAM_OK;
+    }
+  }
   using V = cplx<T>;
   cudaError_t e = launch_rows_forward<T>(pl->rc, static_cast<const RowDev<T>*>(pl->d_rows), pl->P * pl->K, pl->Nr,
                                          static_cast<const V*>(X), y, pl->env, B, static_cast<const V*>(pl->d_twM), st,
@@ -591,6 +657,10 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   if (d->envelope_dtype < 0 || d->envelope_dtype > QTAM_DTYPE_F16) return fail(QTAM_ERR_INVALID_ARG, "unknown envelope dtype");
   if (d->max_window_hz < 0 || d->n_out < 0) return fail(QTAM_ERR_INVALID_ARG, "max_window_hz and n_out must be >= 0");
   if (d->length > ((int64_t)1 << 27)) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "length above 2^27");
+  if (d->short_dft != QTAM_SHORT_DFT_CUDA && d->short_dft != QTAM_SHORT_DFT_TENSOR)
+    return fail(QTAM_ERR_INVALID_ARG, "unknown short_dft");
+  if (d->short_dft == QTAM_SHORT_DFT_TENSOR && (d->compute_dtype != QTAM_DTYPE_F32 || d->n_out != 8192))
+    return fail(QTAM_ERR_UNSUPPORTED_SIZE, "the tensor-core short DFT needs n_out = 8192 and F32 compute");
 
   qtam_plan_s* pl = new (std::nothrow) qtam_plan_s();
   if (!pl) return fail(QTAM_ERR_OUT_OF_MEMORY, "host allocation");
@@ -611,6 +681,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   }
   pl->compute = d->compute_dtype;
   pl->env = d->envelope_dtype;
+  pl->short_dft = d->short_dft;
   pl->tau = d->p_floor_rel >= 0 ? d->p_floor_rel : (pl->compute == QTAM_DTYPE_F64 ? 0.0 : 1e-6);
   pl->P = d->n_q;
   pl->n = pl->N / 2;
@@ -693,7 +764,8 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.threads = threads_for(pl->rc.rp, 0);
   pl->rc.smem = smem_for(pl->rc.rp, 0, pl->cplx_size());
   pl->rc.variant = -1;
-  if (!dbl && pl->all_bisquare()) {   // compile-time variants hard-code the bisquare
+  pl->rc.tensor = pl->short_dft == QTAM_SHORT_DFT_TENSOR && tc_forward_supported(pl->M);
+  if (!dbl && pl->all_bisquare() && !pl->rc.tensor) {   // compile-time variants hard-code the bisquare
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) {
         pl->rc.variant = v;   // first registered variant for this length
@@ -766,7 +838,7 @@ qtam_status qtam_plan_info(qtam_plan_t pl, qtam_plan_info_t* o) {
     o->kept_bins = it->second.kept;
   }
   o->device_bytes = (int64_t)pl->device_bytes;
-  o->row_variant = pl->rc.variant;
+  o->row_variant = pl->rc.tensor ? -2 : pl->rc.variant;
   return QTAM_OK;
 }
 
@@ -778,7 +850,7 @@ qtam_status qtam_plan_variants(qtam_plan_t pl, int32_t* ids, int32_t capacity, i
     ++n;
   };
   push(-1);
-  if (pl->compute == QTAM_DTYPE_F32 && pl->all_bisquare())
+  if (pl->compute == QTAM_DTYPE_F32 && pl->all_bisquare() && !pl->rc.tensor)
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) push(v);
   *count = n;
@@ -789,7 +861,7 @@ qtam_status qtam_plan_set_variant(qtam_plan_t pl, int32_t id) {
   if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
   if (id != -1) {
     const RowVariant* v = row_variant(id);
-    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || !pl->all_bisquare())
+    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || !pl->all_bisquare() || pl->rc.tensor)
       return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length, dtype or window");
   }
   if (id >= 0 && pl->device >= 0) {

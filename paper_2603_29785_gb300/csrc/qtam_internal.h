@@ -53,9 +53,20 @@ struct RowCfg {
   size_t smem;
   int variant;   // index of a compile-time row-kernel variant, -1 = runtime engine
   const void* stw = nullptr;   // stage twiddle tables of that variant
+  // tensor-core short DFT (M = 8192): DFT-64 block operand, DFT-128 cosine and
+  // sine operands, four-step twiddles; used when `tensor` is set
+  int tensor = 0;
+  const void* tcA = nullptr;
+  const void* tcG = nullptr;
+  const void* tcTw = nullptr;
 };
 
 enum EnvKind { ENV_F32 = 0, ENV_F64 = 1, ENV_BF16 = 2, ENV_F16 = 3 };
+
+// Tensor-core forward rows (kernels_tc.cu): M must be 8192, FP32 compute.
+bool tc_forward_supported(int M);
+cudaError_t launch_rows_forward_tc(const RowCfg& c, const RowDev<float>* rows, int n_rows, int64_t Nr,
+                                   const float2* X, void* y, int env, int64_t B, cudaStream_t st, const float* wtab);
 
 // A compile-time row-kernel variant (FP32 compute): fixed M, radix sequence,
 // rows per block and occupancy target.  fwd/inv are indexed by EnvKind.

@@ -28,6 +28,7 @@ STATUS = {
 }
 NORM = {"l2": 0, "paper": 1, "none": 2}
 WINDOW = {"bisquare": 0, "hann": 1, "kaiser": 2, "tukey": 3, "planck": 4}
+SHORT_DFT = {"cuda": 0, "tensor": 1}
 DTYPE = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
 ENV_BYTES = {"f32": 8, "f64": 16, "bf16": 4, "f16": 4}
 
@@ -46,7 +47,7 @@ class qtam_plan_desc(ctypes.Structure):
         ("q_width", ctypes.c_double), ("max_window_hz", ctypes.c_double), ("n_out", ctypes.c_int32),
         ("compute_dtype", ctypes.c_int32), ("envelope_dtype", ctypes.c_int32), ("p_floor_rel", ctypes.c_double),
         ("window_param", ctypes.c_double), ("plane_window", ctypes.POINTER(ctypes.c_int32)),
-        ("plane_window_param", ctypes.POINTER(ctypes.c_double)),
+        ("plane_window_param", ctypes.POINTER(ctypes.c_double)), ("short_dft", ctypes.c_int32),
     ]
 
 
@@ -167,7 +168,8 @@ def _stream(stream) -> int | None:
 # C-named entry points (thin marshalling)
 # ----------------------------------------------------------------------------
 def make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", q_width=0.0, max_window_hz=0.0,
-              n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0, window="bisquare", window_param=0.0):
+              n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0, window="bisquare", window_param=0.0,
+              short_dft="cuda"):
     d = qtam_plan_desc()
     lib().qtam_plan_desc_init(ctypes.byref(d))
     qarr = (ctypes.c_double * len(qs))(*[float(q) for q in qs])
@@ -201,6 +203,7 @@ def make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", 
         keep.append(parr)
         if len(window_param) != len(qs):
             raise ValueError("one window parameter per plane is required")
+    d.short_dft = SHORT_DFT[short_dft]
     d._keep = keep
     return d
 
@@ -416,12 +419,12 @@ class Plan:
 
     def __init__(self, sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", q_width=0.0,
                  max_window_hz=0.0, n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0, device=0,
-                 window="bisquare", window_param=0.0):
+                 window="bisquare", window_param=0.0, short_dft="cuda"):
         self.compute = compute
         self.envelope = envelope or compute
         self.device = int(device)
         self._desc = make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm, q_width, max_window_hz,
-                               n_out, compute, self.envelope, p_floor_rel, window, window_param)
+                               n_out, compute, self.envelope, p_floor_rel, window, window_param, short_dft)
         self.handle = qtam_plan(self._desc, self.device)
         self.info = qtam_plan_info(self.handle)
         self.N = self.info["length"]

@@ -152,6 +152,18 @@ def test_stream_argument_errors():
     assert _err(lambda: qtam.qtam_stream_create(p.handle, 0, 4)) == 8          # default hop is valid
 
 
+def test_tensor_short_dft_options():
+    base = (4096.0, 32768, (8.0, 16.0), 20.0, 2048.0, 64)
+    p = qtam.Plan(*base, n_out=8192, short_dft="tensor", device=-1)
+    assert p.info["row_variant"] == -2 and p.M == 8192
+    assert qtam.qtam_plan_variants(p.handle) == [-1]
+    assert _err(lambda: qtam.Plan(*base, short_dft="tensor", device=-1)) == 2                    # M = 600
+    assert _err(lambda: qtam.Plan(*base, n_out=8192, short_dft="tensor", compute="f64", device=-1)) == 2
+    d = qtam.make_desc(*base)
+    d.short_dft = 5
+    assert _err(lambda: qtam.qtam_plan(d, -1)) == 1
+
+
 def test_f64_defaults():
     p = qtam.Plan(4096, 16384, (8,), 20, 1024, 64, compute="f64", device=-1)
     assert p.info["p_floor_rel"] == 0.0 and p.info["envelope_bytes_per_segment"] == 64 * 250 * 16
