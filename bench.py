@@ -524,36 +524,49 @@ def run_serving(args, local):
 
 
 def run_precision(args, local):
-    """Envelope storage FP32 / BF16 / FP16 on the 64 s workload: error against
-    the FP64 oracle (2 segments) and throughput (64 segments)."""
+    """Precision sweep on the 64 s workload: envelope storage FP32 / BF16 / FP16
+    at M = 4800 (CUDA-core FFTs), and at M = 8192 the CUDA-core runtime engine
+    against the tensor-core short DFT (64 x 128 four-step on tcgen05, BF16
+    operands): error against the FP64 oracle (2 segments), fwd+inv throughput
+    and the envelope stage alone (64 segments)."""
     import torch
     from oracle import qtam_oracle as O
     from paper_2603_29785_gb300 import qtam, tune as qtune
     torch.cuda.set_device(local)
     B = args.batch
+    W = WORKLOAD
     x_host = make_inputs(range(B))
-    g = O.geometry(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"])
-    refs = []
-    for b in range(2):
-        xb = x_host[b].astype(np.float64)
-        Y = O.forward(g, xb)
-        refs.append((Y, O.inverse(g, Y, tau=1e-6)))
+    refs = {}
+    for n_out in (0, 8192):
+        g = O.geometry(W["fs"], W["N"], W["qs"], W["fmin"], W["fmax"], W["K"], n_out=n_out)
+        rr = []
+        for b in range(2):
+            xb = x_host[b].astype(np.float64)
+            Y = O.forward(g, xb)
+            rr.append((Y, O.inverse(g, Y, tau=1e-6)))
+        refs[n_out] = rr
     x = torch.from_numpy(x_host).cuda()
+    st = torch.cuda.current_stream()
+    peaks = {}
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     out = []
-    for env in ("f32", "bf16", "f16"):
-        p = qtam.Plan(WORKLOAD["fs"], WORKLOAD["N"], WORKLOAD["qs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["K"],
-                      envelope=env, device=local)
-        qtune.tune(p, B)
+    for env, n_out, sd in (("f32", 0, "cuda"), ("bf16", 0, "cuda"), ("f16", 0, "cuda"), ("f32", 8192, "cuda"),
+                           ("f32", 8192, "tensor"), ("bf16", 8192, "tensor")):
+        p = qtam.Plan(W["fs"], W["N"], W["qs"], W["fmin"], W["fmax"], W["K"], envelope=env, n_out=n_out,
+                      short_dft=sd, device=local)
+        if sd == "cuda":
+            qtune.tune(p, B)
         y = p.forward(x)
         xh = p.inverse(y)
         torch.cuda.synchronize()
         yv = y[:2].float().cpu().numpy() if env != "f32" else y[:2].cpu().numpy()
         if env != "f32":
             yv = yv[..., 0] + 1j * yv[..., 1]
-        ef = max(float(np.linalg.norm(yv[b] - refs[b][0]) / np.linalg.norm(refs[b][0])) for b in range(2))
-        er = max(float(np.linalg.norm(xh[b].cpu().numpy() - refs[b][1]) / np.linalg.norm(refs[b][1])) for b in range(2))
-        st = torch.cuda.current_stream()
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        rr = refs[n_out]
+        ef = max(float(np.linalg.norm(yv[b] - rr[b][0]) / np.linalg.norm(rr[b][0])) for b in range(2))
+        er = max(float(np.linalg.norm(xh[b].cpu().numpy() - rr[b][1]) / np.linalg.norm(rr[b][1])) for b in range(2))
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         for _ in range(3):
             p.forward(x, y); p.inverse(y, x=xh)
         e[0].record(st)
@@ -562,10 +575,28 @@ def run_precision(args, local):
         e[1].record(st)
         e[1].synchronize()
         ms = e[0].elapsed_time(e[1]) / args.steps
-        out.append({"envelope": env, "forward_rel_err": ef, "roundtrip_rel_err": er,
-                    "msamples_per_s": round(B * WORKLOAD["N"] / ms / 1e3, 1), "ms_per_step": round(ms, 4),
-                    "envelope_bytes_per_segment": p.info["envelope_bytes_per_segment"]})
-    line = {"metric": "QTAM precision sweep: error vs FP64 oracle and Msamples/s per envelope dtype",
+        X = p.spectrum(x)
+        qtam.qtam_stage_envelopes(p.handle, X, B, y, st)
+        e[2].record(st)
+        for _ in range(args.steps):
+            qtam.qtam_stage_envelopes(p.handle, X, B, y, st)
+        e[3].record(st)
+        e[3].synchronize()
+        ms_env = e[2].elapsed_time(e[3]) / args.steps
+        item = {"envelope": env, "M": p.M, "short_dft": sd, "forward_rel_err": ef, "roundtrip_rel_err": er,
+                "msamples_per_s": round(B * W["N"] / ms / 1e3, 1), "ms_per_step": round(ms, 4),
+                "envelope_stage_ms": round(ms_env, 4),
+                "envelope_stage_GB_s": round(B * p.info["envelope_bytes_per_segment"] / (ms_env * 1e-3) / 1e9, 1),
+                "envelope_bytes_per_segment": p.info["envelope_bytes_per_segment"]}
+        if sd == "tensor":
+            # two tcgen05 GEMMs per pair of rows: 128x256x128 + 4 x 128x128x128 multiply-adds
+            flops = B * p.P * p.K / 2 * 2 * (128 * 256 * 128 + 4 * 128 * 128 * 128)
+            tf = flops / (ms_env * 1e-3) / 1e12
+            pk = float(peaks.get("bf16_tflops", 1900.0))
+            item["tensor"] = {"achieved_tflops": round(tf, 1), "peak_tflops": pk, "frac": round(tf / pk, 4),
+                              "peak_source": "measured" if "bf16_tflops" in peaks else "fallback"}
+        out.append(item)
+    line = {"metric": "QTAM precision sweep: error vs FP64 oracle and Msamples/s per envelope dtype and short-DFT engine",
             "value": out[0]["msamples_per_s"], "unit": UNIT, "n_gpus": 1, "dtype": "f32 compute",
             "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "segments": B}, "precision": out}
     print(json.dumps(line), flush=True)

@@ -94,12 +94,14 @@ __global__ void __launch_bounds__(128, 1)
 //           (Re Y, Im Y): Re Y = Re D' Gr - Im D' Gi, Im Y = Re D' Gi + Im D' Gr
 //           with Gr, Gi the cosine / sine DFT-128 matrices (constant, the
 //           minus sign through the MMA's negate-A bit).
-// Shared memory: DFT-64 block 32 KB, Gr 32 KB, Gi 32 KB, one 64 KB operand
-// buffer used first for Z (GEMM A's B) and then for D' (GEMM B's A).
-// Tensor memory: 512 columns, D in 0..255, Y in 256..511.
+// Shared memory: DFT-64 block 32 KB, Gr 32 KB, Gi 32 KB, a 64 KB buffer for
+// Z and one for D'.  Tensor memory: 512 columns, D in 0..255, Y in 256..511.
+// Pipeline per pair i: GEMM A(i) runs while the CUDA cores store the
+// envelopes of pair i-1 from the Y columns; the twiddle pass turns D into D';
+// GEMM B(i) runs while the CUDA cores gather pair i+1 into Z.
 constexpr int kTcM = 8192;
-constexpr int kTcThreads = 256;
-constexpr size_t kTcSmem = 5 * 32768 + 32768;   // constants (96 KB) + operand buffer (64 KB) + 32 KB slack
+constexpr int kTcThreads = 512;
+constexpr size_t kTcSmem = 7 * 32768;   // constants (96 KB) + Z buffer (64 KB) + D' buffer (64 KB)
 
 template <int E> struct TcEnv;
 template <> struct TcEnv<ENV_F32> {
@@ -120,183 +122,222 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// Band gather + window of one pair of rows into Z (GEMM A's B operand,
+// [256 c = 128 r + j2][128 k = Re j1 | Im j1]).  Thread (r, j2, h) =
+// ((tid >> 7) & 1, tid & 127, tid >> 8) loads Z[r][128 j1 + j2] for j1 in
+// 32 h .. 32 h + 31: a warp's loads are 32 consecutive bins, its 16-byte
+// stores one core-matrix row each.
+__device__ __forceinline__ void tc_fill_z(unsigned char* sZ, int64_t pr, int64_t n_units, int n_rows, int64_t Nr,
+                                          const RowDev<float>* __restrict__ rows, const float2* __restrict__ X,
+                                          const float* __restrict__ wtab) {
+  const int tid = threadIdx.x;
+  const int r = (tid >> 7) & 1, j2 = tid & 127, h0 = 4 * (tid >> 8);
+  const int64_t u = 2 * pr + r;
+  const bool valid = u < n_units;
+  const int64_t seg = valid ? u / n_rows : 0;
+  const int row = valid ? (int)(u - seg * n_rows) : 0;
+  const RowDev<float> rd = rows[row];
+  const int64_t nhalf = Nr - 1;
+  const int dhi = (int)min((int64_t)rd.h, nhalf - rd.kc);
+  const int dlo = (int)max((int64_t)-rd.h, (int64_t)-rd.kc);
+  const int mlo = kTcM + dlo;
+  const float2* Xs = X + seg * Nr + rd.kc;
+  const bool tab = wtab != nullptr && rd.woff >= 0;
+  const unsigned c = 128u * r + j2;
+#pragma unroll 2
+  for (int o = h0; o < h0 + 4; ++o) {
+    float re[8], im[8];
+#pragma unroll
+    for (int e = 0; e < 8; ++e) {
+      const int j = 128 * (8 * o + e) + j2;
+      const bool lo = j <= dhi, hi = j >= mlo;
+      const int d = lo ? j : j - kTcM;
+      float2 v = make_float2(0.f, 0.f);
+      if (valid && (lo || hi)) v = Xs[d];
+      const int a = min(d < 0 ? -d : d, rd.h);
+      float w;
+      if (tab) {
+        w = rd.c_fwd * wtab[rd.woff + a];
+      } else {
+        const float uu = (float)((rd.h - a) * (rd.h + a)) * rd.kw_fwd;
+        w = uu * uu;
+      }
+      re[e] = v.x * w;
+      im[e] = v.y * w;
+    }
+    *reinterpret_cast<uint4*>(sZ + tc::cm_offset(c, 8 * o, 128)) = make_uint4(
+        pack_bf16(re[0], re[1]), pack_bf16(re[2], re[3]), pack_bf16(re[4], re[5]), pack_bf16(re[6], re[7]));
+    *reinterpret_cast<uint4*>(sZ + tc::cm_offset(c, 64 + 8 * o, 128)) = make_uint4(
+        pack_bf16(im[0], im[1]), pack_bf16(im[2], im[3]), pack_bf16(im[4], im[5]), pack_bf16(im[6], im[7]));
+  }
+}
+
+// Envelopes of pair pr from tensor memory (Re Y in columns 256.., Im Y in
+// 384..) to y[u][n1 + 64 n2]; lanes are rows 64 r + n1, so a warp's stores
+// are 32 consecutive envelope samples.
+template <int E>
+__device__ __forceinline__ void tc_store_y(uint32_t tbase, int64_t pr, int64_t n_units,
+                                           typename TcEnv<E>::S* __restrict__ y) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q4 = warp & 3, quarter = warp >> 2;   // lane quarter, quarter of the n2 range
+  const int r = q4 >> 1, n1 = 32 * (q4 & 1) + lane;
+  const int64_t u = 2 * pr + r;
+  if (u >= n_units) return;   // r is uniform per warp: whole warps skip the collective loads
+  typename TcEnv<E>::S* yu = y + u * kTcM + n1;
+  const uint32_t lrow = (uint32_t)(32 * q4) << 16;
+#pragma unroll 1
+  for (int q = 0; q < 2; ++q) {
+    const int n20 = 32 * quarter + 16 * q;
+    float vr[16], vi[16];
+    tc::tmem_ld16_nowait(tbase + lrow + 256u + (uint32_t)n20, vr);
+    tc::tmem_ld16_nowait(tbase + lrow + 384u + (uint32_t)n20, vi);
+    tc::tmem_wait_ld(vr, vi);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) __stcs(yu + 64 * (n20 + e), TcEnv<E>::to(vr[e], vi[e]));
+  }
+}
+
 template <int E>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_rows_forward_tc(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
                       typename TcEnv<E>::S* __restrict__ y, int64_t n_units, const uint4* __restrict__ tabA,
                       const uint4* __restrict__ tabG, const float2* __restrict__ tw, const float* __restrict__ wtab) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbarA, mbarB;
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
   unsigned char* sA = sm;                 // DFT-64 block, [128][128] K-major
   unsigned char* sGr = sm + 32768;        // [128 n2][128 j2]
   unsigned char* sGi = sm + 65536;
-  unsigned char* sD = sm + 98304;         // Z as [256 c][128 k], then D' as [128 m][256 k]
+  unsigned char* sZ = sm + 98304;         // Z of the next pair, [256 c][128 k]
+  unsigned char* sDp = sm + 163840;       // D' of the current pair, [128 m][256 k]
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int i = tid; i < 2048; i += kTcThreads) reinterpret_cast<uint4*>(sA)[i] = tabA[i];
   for (int i = tid; i < 4096; i += kTcThreads) reinterpret_cast<uint4*>(sGr)[i] = tabG[i];
-  if (warp == 0) {
+  if (warp == 0) {   // 512 columns: one CTA per SM (the shared memory admits no second one)
     tc::tmem_alloc(&tslot, 512);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
-    tc::mbar_init(&mbar, 1);
+    tc::mbar_init(&mbarA, 1);
+    tc::mbar_init(&mbarB, 1);
     abort_flag = 0;
   }
+  // twiddle pass: warp (q4, cq) handles D lanes 32 q4.. (rows 2 n1 + re/im) and
+  // columns 64 cq .. 64 cq + 63 (row r = cq >> 1, j2 from 64 (cq & 1)); the
+  // twiddle e^{2 pi i n1 j2 / 8192} is evaluated from the exact integer n1 j2
+  // with the SFU sine/cosine (absolute error ~1e-6, far below the BF16
+  // rounding of the result)
+  const int q4 = warp & 3, cq = warp >> 2;
+  const int rh = cq >> 1, j2b = 64 * (cq & 1);
+  const int n1 = 16 * q4 + (lane >> 1), part = lane & 1;
+  constexpr float kAng = 6.28318530717958647692f / (float)kTcM;
+  (void)tw;
+  const int64_t n_pairs = (n_units + 1) >> 1;
+  int64_t pr = blockIdx.x;
+  if (pr < n_pairs) tc_fill_z(sZ, pr, n_units, n_rows, Nr, rows, X, wtab);
   tc::fence_smem_to_async();
   tc::fence_before_sync();
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tslot;
-  const uint32_t aA = tc::smem_addr(sA), aGr = tc::smem_addr(sGr), aGi = tc::smem_addr(sGi), aD = tc::smem_addr(sD);
-  const int64_t nhalf = Nr - 1;
-  const int64_t n_pairs = (n_units + 1) >> 1;
-  uint32_t phase = 0;
-  bool pending = false;
+  const uint32_t aA = tc::smem_addr(sA), aGr = tc::smem_addr(sGr), aGi = tc::smem_addr(sGi);
+  const uint32_t aZ = tc::smem_addr(sZ), aDp = tc::smem_addr(sDp);
+  uint32_t phA = 0, phB = 0;
+  bool pendA = false, pendB = false;
+  int64_t prev = -1;
 
-  for (int64_t pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
-    // ---- 1. band gather + window -> Z (GEMM A's B operand) ----
-    {
-      const int r = tid >> 7, j2 = tid & 127;
-      const int64_t u = 2 * pr + r;
-      const bool valid = u < n_units;
-      const int64_t seg = valid ? u / n_rows : 0;
-      const int row = valid ? (int)(u - seg * n_rows) : 0;
-      const RowDev<float> rd = rows[row];
-      const int dhi = (int)min((int64_t)rd.h, nhalf - rd.kc);
-      const int dlo = (int)max((int64_t)-rd.h, (int64_t)-rd.kc);
-      const int mlo = kTcM + dlo;
-      const float2* Xs = X + seg * Nr + rd.kc;
-      const bool tab = wtab != nullptr && rd.woff >= 0;
-      const unsigned c = 128u * r + j2;
-#pragma unroll 2
-      for (int o = 0; o < 8; ++o) {
-        float re[8], im[8];
-#pragma unroll
-        for (int e = 0; e < 8; ++e) {
-          const int j = 128 * (8 * o + e) + j2;
-          const bool lo = j <= dhi, hi = j >= mlo;
-          const int d = lo ? j : j - kTcM;
-          float2 v = make_float2(0.f, 0.f);
-          if (valid && (lo || hi)) v = Xs[d];
-          const int a = min(d < 0 ? -d : d, rd.h);
-          float w;
-          if (tab) {
-            w = rd.c_fwd * wtab[rd.woff + a];
-          } else {
-            const float uu = (float)((rd.h - a) * (rd.h + a)) * rd.kw_fwd;
-            w = uu * uu;
-          }
-          re[e] = v.x * w;
-          im[e] = v.y * w;
-        }
-        const uint4 pr4 = make_uint4(pack_bf16(re[0], re[1]), pack_bf16(re[2], re[3]), pack_bf16(re[4], re[5]),
-                                     pack_bf16(re[6], re[7]));
-        const uint4 pi4 = make_uint4(pack_bf16(im[0], im[1]), pack_bf16(im[2], im[3]), pack_bf16(im[4], im[5]),
-                                     pack_bf16(im[6], im[7]));
-        *reinterpret_cast<uint4*>(sD + tc::cm_offset(c, 8 * o, 128)) = pr4;
-        *reinterpret_cast<uint4*>(sD + tc::cm_offset(c, 64 + 8 * o, 128)) = pi4;
-      }
-    }
-    tc::fence_smem_to_async();
-    tc::fence_before_sync();
-    __syncthreads();
-    tc::fence_after_sync();
-    // ---- 2. GEMM A: D[tmem 0..255] = DFT64 * Z ----
+  for (; pr < n_pairs; pr += gridDim.x) {
+    // ---- GEMM A: D[tmem 0..255] = DFT64 * Z ----
     if (tid == 0) {
       const uint32_t idesc = tc::make_idesc_bf16(128, 256);
 #pragma unroll
       for (int s = 0; s < 8; ++s)
-        tc::mma_bf16(tbase, tc::make_sdesc(aA + 256u * s, 128u, 2048u), tc::make_sdesc(aD + 256u * s, 128u, 2048u),
+        tc::mma_bf16(tbase, tc::make_sdesc(aA + 256u * s, 128u, 2048u), tc::make_sdesc(aZ + 256u * s, 128u, 2048u),
                      idesc, s > 0);
-      tc::mma_commit(&mbar);
+      tc::mma_commit(&mbarA);
     }
-    pending = true;
-    if (!tc::mbar_wait_bounded(&mbar, phase, tc::kWaitCycles)) abort_flag = 1;
+    pendA = true;
+    // ... overlapped with the previous pair's envelope stores (Y columns are not touched by GEMM A)
+    if (prev >= 0) tc_store_y<E>(tbase, prev, n_units, y);
+    if (!tc::mbar_wait_bounded(&mbarA, phA, tc::kWaitCycles)) abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
     if (abort_flag) break;
-    phase ^= 1u;
-    pending = false;
-    // ---- 3. twiddle D -> D' (GEMM B's A operand, [128 m = 64 r + n1][256 k = Re j2 | Im j2]) ----
+    phA ^= 1u;
+    pendA = false;
+    // ---- twiddle: D -> D' ([128 m = 64 r + n1][256 k = Re j2 | Im j2]) ----
     {
-      const int q4 = warp & 3, rh = warp >> 2;
-      const int n1 = 16 * q4 + (lane >> 1), part = lane & 1;
       const unsigned m = 64u * rh + n1;
-      const float2* twr = tw + n1 * 128;
-#pragma unroll 1
-      for (int q = 0; q < 8; ++q) {
-        float v[16];
-        tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + (uint32_t)(128 * rh + 16 * q), v);
+      const uint32_t lrow = (uint32_t)(32 * q4) << 16;
+#pragma unroll
+      for (int q2 = 0; q2 < 4; q2 += 2) {
+        float va[16], vb[16];
+        tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(64 * cq + 16 * q2), va);
+        tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(64 * cq + 16 * q2 + 16), vb);
+        tc::tmem_wait_ld(va, vb);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+        const int q = q2 + h;
+        const float* v = h ? vb : va;
         float o[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
           const float p = __shfl_xor_sync(0xffffffffu, v[e], 1);
           const float re = part ? p : v[e], im = part ? v[e] : p;
-          const float2 t = twr[16 * q + e];
-          o[e] = part ? fmaf(re, t.y, im * t.x) : fmaf(re, t.x, -im * t.y);
+          float ty, tx;
+          __sincosf(kAng * (float)(n1 * (j2b + 16 * q + e)), &ty, &tx);
+          o[e] = part ? fmaf(re, ty, im * tx) : fmaf(re, tx, -im * ty);
         }
-        const unsigned k0 = 128u * part + 16u * q;
-        *reinterpret_cast<uint4*>(sD + tc::cm_offset(m, k0, 256)) =
+        const unsigned k0 = 128u * part + (unsigned)(j2b + 16 * q);
+        *reinterpret_cast<uint4*>(sDp + tc::cm_offset(m, k0, 256)) =
             make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]), pack_bf16(o[4], o[5]), pack_bf16(o[6], o[7]));
-        *reinterpret_cast<uint4*>(sD + tc::cm_offset(m, k0 + 8, 256)) = make_uint4(
+        *reinterpret_cast<uint4*>(sDp + tc::cm_offset(m, k0 + 8, 256)) = make_uint4(
             pack_bf16(o[8], o[9]), pack_bf16(o[10], o[11]), pack_bf16(o[12], o[13]), pack_bf16(o[14], o[15]));
+        }
       }
     }
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
-    // ---- 4. GEMM B: Re Y [tmem 256..383], Im Y [384..511] ----
+    // ---- GEMM B: Re Y [tmem 256..383], Im Y [384..511] ----
     if (tid == 0) {
       const uint32_t id = tc::make_idesc_bf16(128, 128), idn = tc::make_idesc_bf16(128, 128, true);
       const uint32_t tRe = tbase + 256u, tIm = tbase + 384u;
 #pragma unroll
       for (int s = 0; s < 8; ++s) {   // Re D' * Gr, Re D' * Gi
-        const uint64_t a = tc::make_sdesc(aD + 256u * s, 128u, 4096u);
+        const uint64_t a = tc::make_sdesc(aDp + 256u * s, 128u, 4096u);
         tc::mma_bf16(tRe, a, tc::make_sdesc(aGr + 256u * s, 128u, 2048u), id, s > 0);
         tc::mma_bf16(tIm, a, tc::make_sdesc(aGi + 256u * s, 128u, 2048u), id, s > 0);
       }
 #pragma unroll
       for (int s = 0; s < 8; ++s) {   // - Im D' * Gi, + Im D' * Gr
-        const uint64_t a = tc::make_sdesc(aD + 256u * (8 + s), 128u, 4096u);
+        const uint64_t a = tc::make_sdesc(aDp + 256u * (8 + s), 128u, 4096u);
         tc::mma_bf16(tRe, a, tc::make_sdesc(aGi + 256u * s, 128u, 2048u), idn, 1u);
         tc::mma_bf16(tIm, a, tc::make_sdesc(aGr + 256u * s, 128u, 2048u), id, 1u);
       }
-      tc::mma_commit(&mbar);
+      tc::mma_commit(&mbarB);
     }
-    pending = true;
-    if (!tc::mbar_wait_bounded(&mbar, phase, tc::kWaitCycles)) abort_flag = 1;
-    tc::fence_after_sync();
-    __syncthreads();
-    if (abort_flag) break;
-    phase ^= 1u;
-    pending = false;
-    // ---- 5. envelopes out: y[u][n1 + 64 n2] ----
-    {
-      const int q4 = warp & 3, half = warp >> 2;
-      const int r = q4 >> 1, n1 = 32 * (q4 & 1) + lane;
-      const int64_t u = 2 * pr + r;
-      if (u < n_units) {
-        typename TcEnv<E>::S* yu = y + u * kTcM + n1;
-#pragma unroll 1
-        for (int q = 0; q < 4; ++q) {
-          const int n20 = 64 * half + 16 * q;
-          float vr[16], vi[16];
-          tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + 256u + (uint32_t)n20, vr);
-          tc::tmem_ld16(tbase + ((uint32_t)(32 * q4) << 16) + 384u + (uint32_t)n20, vi);
-#pragma unroll
-          for (int e = 0; e < 16; ++e) __stcs(yu + 64 * (n20 + e), TcEnv<E>::to(vr[e], vi[e]));
-        }
-      }   // r is uniform per warp, so the warp-collective loads are skipped by whole warps only
-    }
+    pendB = true;
+    // ... overlapped with the next pair's band gather (GEMM A has finished reading Z)
+    const int64_t nx = pr + gridDim.x;
+    if (nx < n_pairs) tc_fill_z(sZ, nx, n_units, n_rows, Nr, rows, X, wtab);
+    if (!tc::mbar_wait_bounded(&mbarB, phB, tc::kWaitCycles)) abort_flag = 1;
+    tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
+    tc::fence_after_sync();
+    if (abort_flag) break;
+    phB ^= 1u;
+    pendB = false;
+    prev = pr;
   }
+  if (!abort_flag && prev >= 0) tc_store_y<E>(tbase, prev, n_units, y);
   if (abort_flag) {
     if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
-    if (pending) tc::mbar_wait_bounded(&mbar, phase, tc::kWaitCycles);
+    if (pendA) tc::mbar_wait_bounded(&mbarA, phA, tc::kWaitCycles);
+    if (pendB) tc::mbar_wait_bounded(&mbarB, phB, tc::kWaitCycles);
   }
   tc::fence_before_sync();
   __syncthreads();
