@@ -555,8 +555,7 @@ def run_precision(args, local):
                            ("f32", 8192, "tensor"), ("bf16", 8192, "tensor")):
         p = qtam.Plan(W["fs"], W["N"], W["qs"], W["fmin"], W["fmax"], W["K"], envelope=env, n_out=n_out,
                       short_dft=sd, device=local)
-        if sd == "cuda":
-            qtune.tune(p, B)
+        qtune.tune(p, B)          # CUDA-core variants (the inverse, and the forward of "cuda" plans)
         y = p.forward(x)
         xh = p.inverse(y)
         torch.cuda.synchronize()

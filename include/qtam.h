@@ -133,8 +133,9 @@ typedef struct {
   double kappa;                   /* max over kept bins of max_k W_k / P (all planes) */
   int64_t kept_bins;              /* |F_tau| for all planes */
   int64_t device_bytes;           /* bytes of resident plan tables on the device */
-  int32_t row_variant;            /* row-kernel variant in use (-1: runtime engine; -2: tensor-core
-                                     forward with the runtime engine for the inverse) */
+  int32_t row_variant;            /* CUDA-core row-kernel variant in use (-1: runtime engine); with
+                                     the tensor-core short DFT it serves the inverse only */
+  int32_t short_dft;              /* QTAM_SHORT_DFT_* engine of the envelope stage */
 } qtam_plan_info_t;
 
 /* Fill *d with defaults: bisquare, L2 norm, q_width sqrt(11), automatic clamp

@@ -379,6 +379,9 @@ const RowVariant kVariants[] = {
     QTAM_V(300, 4, 2, 4, 3, 25),
     QTAM_V(150, 4, 2, 6, 25),
     QTAM_V(75, 5, 2, 3, 25),
+    QTAM_V(8192, 0, 1, 16, 16, 32),
+    QTAM_V(8192, 0, 1, 32, 16, 16),
+    QTAM_V(8192, 0, 1, 16, 32, 16),
 };
 #undef QTAM_V
 

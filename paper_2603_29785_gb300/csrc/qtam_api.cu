@@ -765,7 +765,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.smem = smem_for(pl->rc.rp, 0, pl->cplx_size());
   pl->rc.variant = -1;
   pl->rc.tensor = pl->short_dft == QTAM_SHORT_DFT_TENSOR && tc_forward_supported(pl->M);
-  if (!dbl && pl->all_bisquare() && !pl->rc.tensor) {   // compile-time variants hard-code the bisquare
+  if (!dbl && pl->all_bisquare()) {   // compile-time variants hard-code the bisquare
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) {
         pl->rc.variant = v;   // first registered variant for this length
@@ -838,7 +838,8 @@ qtam_status qtam_plan_info(qtam_plan_t pl, qtam_plan_info_t* o) {
     o->kept_bins = it->second.kept;
   }
   o->device_bytes = (int64_t)pl->device_bytes;
-  o->row_variant = pl->rc.tensor ? -2 : pl->rc.variant;
+  o->row_variant = pl->rc.variant;
+  o->short_dft = pl->rc.tensor ? QTAM_SHORT_DFT_TENSOR : QTAM_SHORT_DFT_CUDA;
   return QTAM_OK;
 }
 
@@ -850,7 +851,7 @@ qtam_status qtam_plan_variants(qtam_plan_t pl, int32_t* ids, int32_t capacity, i
     ++n;
   };
   push(-1);
-  if (pl->compute == QTAM_DTYPE_F32 && pl->all_bisquare() && !pl->rc.tensor)
+  if (pl->compute == QTAM_DTYPE_F32 && pl->all_bisquare())
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) push(v);
   *count = n;
@@ -861,7 +862,7 @@ qtam_status qtam_plan_set_variant(qtam_plan_t pl, int32_t id) {
   if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
   if (id != -1) {
     const RowVariant* v = row_variant(id);
-    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || !pl->all_bisquare() || pl->rc.tensor)
+    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || !pl->all_bisquare())
       return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length, dtype or window");
   }
   if (id >= 0 && pl->device >= 0) {

@@ -155,8 +155,9 @@ def test_stream_argument_errors():
 def test_tensor_short_dft_options():
     base = (4096.0, 32768, (8.0, 16.0), 20.0, 2048.0, 64)
     p = qtam.Plan(*base, n_out=8192, short_dft="tensor", device=-1)
-    assert p.info["row_variant"] == -2 and p.M == 8192
-    assert qtam.qtam_plan_variants(p.handle) == [-1]
+    assert p.info["short_dft"] == 1 and p.M == 8192
+    assert len(qtam.qtam_plan_variants(p.handle)) == 4      # runtime engine + 3 compile-time inverse variants
+    assert qtam.Plan(*base, device=-1).info["short_dft"] == 0
     assert _err(lambda: qtam.Plan(*base, short_dft="tensor", device=-1)) == 2                    # M = 600
     assert _err(lambda: qtam.Plan(*base, n_out=8192, short_dft="tensor", compute="f64", device=-1)) == 2
     d = qtam.make_desc(*base)

@@ -21,6 +21,7 @@ GEOMS = {
     300: (4096.0, 16384, (8.0, 16.0, 32.0), 20.0, 2048.0, 128),
     150: (4096.0, 8192, (8.0, 16.0, 32.0), 20.0, 2048.0, 128),
     75: (4096.0, 4096, (8.0, 16.0, 32.0), 20.0, 2048.0, 128),
+    8192: (4096.0, 262144, (4.0, 8.0, 16.0, 32.0, 64.0), 20.0, 2048.0, 128, 8192),   # n_out = 8192
 }
 
 
@@ -30,10 +31,11 @@ def rel(a, b):
 
 @pytest.mark.parametrize("M", sorted(GEOMS))
 def test_every_variant_matches_oracle(M):
-    fs, N, qs, fmin, fmax, K = GEOMS[M]
-    p = qtam.Plan(fs, N, qs, fmin, fmax, K, device=0)
+    fs, N, qs, fmin, fmax, K = GEOMS[M][:6]
+    n_out = GEOMS[M][6] if len(GEOMS[M]) > 6 else 0
+    p = qtam.Plan(fs, N, qs, fmin, fmax, K, n_out=n_out, device=0)
     assert p.M == M
-    g = O.geometry(fs, N, qs, fmin, fmax, K)
+    g = O.geometry(fs, N, qs, fmin, fmax, K, n_out=n_out)
     variants = qtam.qtam_plan_variants(p.handle)
     assert variants[0] == -1 and len(variants) >= 2, variants
     x = synth.glitchy_segment(M, N, fs, chirp=True).astype(np.float64)
