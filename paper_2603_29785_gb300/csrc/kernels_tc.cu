@@ -28,10 +28,19 @@ __global__ void __launch_bounds__(128, 1)
   unsigned char* sA = sm;
   unsigned char* sB = sm + 128 * K * 2;
   const int K8 = K >> 3;
-  for (int ch = threadIdx.x; ch < 128 * K8; ch += blockDim.x) {
-    const int row = ch / K8, k8 = ch - row * K8;
-    *reinterpret_cast<uint4*>(sA + tc::cm_offset(row, k8 * 8, K)) =
-        *reinterpret_cast<const uint4*>(A + (size_t)row * K + k8 * 8);
+  if (flags & 4u) {   // A in the M-major layout: 8 consecutive rows of one column per 16 bytes
+    for (int ch = threadIdx.x; ch < 16 * K; ch += blockDim.x) {
+      const int k = ch / 16, g = ch - k * 16;
+      __align__(16) uint16_t v[8];
+      for (int i = 0; i < 8; ++i) v[i] = A[(size_t)(8 * g + i) * K + k];
+      *reinterpret_cast<uint4*>(sA + tc::cm_offset_mn(8 * g, k, K)) = *reinterpret_cast<const uint4*>(v);
+    }
+  } else {
+    for (int ch = threadIdx.x; ch < 128 * K8; ch += blockDim.x) {
+      const int row = ch / K8, k8 = ch - row * K8;
+      *reinterpret_cast<uint4*>(sA + tc::cm_offset(row, k8 * 8, K)) =
+          *reinterpret_cast<const uint4*>(A + (size_t)row * K + k8 * 8);
+    }
   }
   for (int ch = threadIdx.x; ch < N * K8; ch += blockDim.x) {
     const int row = ch / K8, k8 = ch - row * K8;
@@ -51,7 +60,7 @@ __global__ void __launch_bounds__(128, 1)
   tc::fence_after_sync();
   const uint32_t tbase = tslot;
   if (threadIdx.x == 0) {
-    const uint32_t idesc = tc::make_idesc_bf16(128, N, flags & 1u, flags & 2u);
+    const uint32_t idesc = tc::make_idesc_bf16(128, N, flags & 1u, flags & 2u, flags & 4u);
     const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB), sbo = (uint32_t)K8 * 128u;
     for (int s = 0; s < K / 16; ++s)
       tc::mma_bf16(tbase, tc::make_sdesc(a0 + 256u * s, 128u, sbo), tc::make_sdesc(b0 + 256u * s, 128u, sbo), idesc,
@@ -87,15 +96,18 @@ __global__ void __launch_bounds__(128, 1)
 //   Y[n1+64n2] = sum_j2 D'[n1][j2] e^{+2 pi i j2 n2/128}        GEMM B (tensor cores)
 // Complex products are real GEMMs on (re, im) blocks with BF16 operands and
 // FP32 accumulation in tensor memory:
-//   GEMM A: M = 128 rows (2 n1 + re/im), K = 128 (j1 of Re Z, j1 of Im Z),
-//           N = 256 columns (j2 of row 0, j2 of row 1); A = the DFT-64 block
-//           matrix (constant), B = Z written by the band gather.
+//   GEMM A (one per row r of the pair): M = 128 (j2), K = 128 (j1 of Re Z,
+//           j1 of Im Z), N = 128 (Re D for n1 < 64, Im D); A = Z^T written by
+//           the band gather, B = the DFT-64 block matrix (constant).  A lane
+//           (thread) of the result holds whole complex values D[n1][j2].
 //   GEMM B: M = 128 rows (64 r + n1), K = 128 per part, N = 128 + 128
 //           (Re Y, Im Y): Re Y = Re D' Gr - Im D' Gi, Im Y = Re D' Gi + Im D' Gr
 //           with Gr, Gi the cosine / sine DFT-128 matrices (constant, the
-//           minus sign through the MMA's negate-A bit).
+//           minus sign through the MMA's negate-A bit); D' is stored M-major,
+//           so the thread owning column j2 writes 8 rows per 16-byte store.
 // Shared memory: DFT-64 block 32 KB, Gr 32 KB, Gi 32 KB, a 64 KB buffer for
-// Z and one for D'.  Tensor memory: 512 columns, D in 0..255, Y in 256..511.
+// Z and one for D'.  Tensor memory: 512 columns, D of row r in 128 r ..
+// 128 r + 127, Y in 256..511.
 // Pipeline per pair i: GEMM A(i) runs while the CUDA cores store the
 // envelopes of pair i-1 from the Y columns; the twiddle pass turns D into D';
 // GEMM B(i) runs while the CUDA cores gather pair i+1 into Z.
@@ -146,6 +158,13 @@ __device__ __forceinline__ void tc_fill_z(unsigned char* sZ, int64_t pr, int64_t
   const unsigned c = 128u * r + j2;
 #pragma unroll 2
   for (int o = h0; o < h0 + 4; ++o) {
+    // octets wholly outside the band (for every lane of the warp) are zeros
+    const int jmin = 1024 * o + j2;
+    if (!__any_sync(0xffffffffu, valid && (jmin <= dhi || jmin + 896 >= mlo))) {
+      *reinterpret_cast<uint4*>(sZ + tc::cm_offset(c, 8 * o, 128)) = make_uint4(0u, 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(sZ + tc::cm_offset(c, 64 + 8 * o, 128)) = make_uint4(0u, 0u, 0u, 0u);
+      continue;
+    }
     float re[8], im[8];
 #pragma unroll
     for (int e = 0; e < 8; ++e) {
@@ -201,16 +220,16 @@ template <int E>
 __global__ void __launch_bounds__(kTcThreads, 1)
     k_rows_forward_tc(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
                       typename TcEnv<E>::S* __restrict__ y, int64_t n_units, const uint4* __restrict__ tabA,
-                      const uint4* __restrict__ tabG, const float2* __restrict__ tw, const float* __restrict__ wtab) {
+                      const uint4* __restrict__ tabG, const float* __restrict__ wtab) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbarA, mbarB;
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
-  unsigned char* sA = sm;                 // DFT-64 block, [128][128] K-major
+  unsigned char* sA = sm;                 // DFT-64 block, [128 n][128 k] K-major (GEMM A's B)
   unsigned char* sGr = sm + 32768;        // [128 n2][128 j2]
   unsigned char* sGi = sm + 65536;
-  unsigned char* sZ = sm + 98304;         // Z of the next pair, [256 c][128 k]
-  unsigned char* sDp = sm + 163840;       // D' of the current pair, [128 m][256 k]
+  unsigned char* sZ = sm + 98304;         // Z^T of the next pair: row r at 32 KB r, [128 j2][128 k] K-major
+  unsigned char* sDp = sm + 163840;       // D' of the current pair, [128 m][256 k] M-major
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   for (int i = tid; i < 2048; i += kTcThreads) reinterpret_cast<uint4*>(sA)[i] = tabA[i];
   for (int i = tid; i < 4096; i += kTcThreads) reinterpret_cast<uint4*>(sGr)[i] = tabG[i];
@@ -223,16 +242,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::mbar_init(&mbarB, 1);
     abort_flag = 0;
   }
-  // twiddle pass: warp (q4, cq) handles D lanes 32 q4.. (rows 2 n1 + re/im) and
-  // columns 64 cq .. 64 cq + 63 (row r = cq >> 1, j2 from 64 (cq & 1)); the
-  // twiddle e^{2 pi i n1 j2 / 8192} is evaluated from the exact integer n1 j2
-  // with the SFU sine/cosine (absolute error ~1e-6, far below the BF16
-  // rounding of the result)
-  const int q4 = warp & 3, cq = warp >> 2;
-  const int rh = cq >> 1, j2b = 64 * (cq & 1);
-  const int n1 = 16 * q4 + (lane >> 1), part = lane & 1;
+  // twiddle pass: warp (q4, cg) handles lanes j2 = 32 q4 + lane of row
+  // r = cg >> 1, n1 = 32 (cg & 1) .. + 31; the twiddle e^{2 pi i n1 j2 / 8192}
+  // is evaluated from the exact integer n1 j2 with the SFU sine/cosine
+  // (absolute error ~1e-6, far below the BF16 rounding of the result)
+  const int q4 = warp & 3, cg = warp >> 2;
+  const int j2 = 32 * q4 + lane, rr = cg >> 1, nb = 32 * (cg & 1);
   constexpr float kAng = 6.28318530717958647692f / (float)kTcM;
-  (void)tw;
   const int64_t n_pairs = (n_units + 1) >> 1;
   int64_t pr = blockIdx.x;
   if (pr < n_pairs) tc_fill_z(sZ, pr, n_units, n_rows, Nr, rows, X, wtab);
@@ -248,13 +264,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   int64_t prev = -1;
 
   for (; pr < n_pairs; pr += gridDim.x) {
-    // ---- GEMM A: D[tmem 0..255] = DFT64 * Z ----
+    // ---- GEMM A: D_r[tmem 128 r ..] = Z_r^T * DFT64^T, r = 0, 1 ----
     if (tid == 0) {
-      const uint32_t idesc = tc::make_idesc_bf16(128, 256);
+      const uint32_t idesc = tc::make_idesc_bf16(128, 128);
 #pragma unroll
-      for (int s = 0; s < 8; ++s)
-        tc::mma_bf16(tbase, tc::make_sdesc(aA + 256u * s, 128u, 2048u), tc::make_sdesc(aZ + 256u * s, 128u, 2048u),
-                     idesc, s > 0);
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+          tc::mma_bf16(tbase + 128u * r, tc::make_sdesc(aZ + 32768u * r + 256u * s, 128u, 2048u),
+                       tc::make_sdesc(aA + 256u * s, 128u, 2048u), idesc, s > 0);
       tc::mma_commit(&mbarA);
     }
     pendA = true;
@@ -266,34 +284,33 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (abort_flag) break;
     phA ^= 1u;
     pendA = false;
-    // ---- twiddle: D -> D' ([128 m = 64 r + n1][256 k = Re j2 | Im j2]) ----
+    // ---- twiddle: D -> D' ([128 m = 64 r + n1][256 k = Re j2 | Im j2], M-major) ----
     {
-      const unsigned m = 64u * rh + n1;
       const uint32_t lrow = (uint32_t)(32 * q4) << 16;
-#pragma unroll
-      for (int q2 = 0; q2 < 4; q2 += 2) {
-        float va[16], vb[16];
-        tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(64 * cq + 16 * q2), va);
-        tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(64 * cq + 16 * q2 + 16), vb);
-        tc::tmem_wait_ld(va, vb);
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-        const int q = q2 + h;
-        const float* v = h ? vb : va;
-        float o[16];
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int n10 = nb + 16 * h;
+        float vr[16], vi[16];
+        tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(128 * rr + n10), vr);
+        tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(128 * rr + 64 + n10), vi);
+        tc::tmem_wait_ld(vr, vi);
+        float orr[16], oi[16];
 #pragma unroll
         for (int e = 0; e < 16; ++e) {
-          const float p = __shfl_xor_sync(0xffffffffu, v[e], 1);
-          const float re = part ? p : v[e], im = part ? v[e] : p;
           float ty, tx;
-          __sincosf(kAng * (float)(n1 * (j2b + 16 * q + e)), &ty, &tx);
-          o[e] = part ? fmaf(re, ty, im * tx) : fmaf(re, tx, -im * ty);
+          __sincosf(kAng * (float)((n10 + e) * j2), &ty, &tx);
+          orr[e] = fmaf(vr[e], tx, -vi[e] * ty);
+          oi[e] = fmaf(vr[e], ty, vi[e] * tx);
         }
-        const unsigned k0 = 128u * part + (unsigned)(j2b + 16 * q);
-        *reinterpret_cast<uint4*>(sDp + tc::cm_offset(m, k0, 256)) =
-            make_uint4(pack_bf16(o[0], o[1]), pack_bf16(o[2], o[3]), pack_bf16(o[4], o[5]), pack_bf16(o[6], o[7]));
-        *reinterpret_cast<uint4*>(sDp + tc::cm_offset(m, k0 + 8, 256)) = make_uint4(
-            pack_bf16(o[8], o[9]), pack_bf16(o[10], o[11]), pack_bf16(o[12], o[13]), pack_bf16(o[14], o[15]));
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const int m0 = 64 * rr + n10 + 8 * g;
+          *reinterpret_cast<uint4*>(sDp + tc::cm_offset_mn(m0, j2, 256)) =
+              make_uint4(pack_bf16(orr[8 * g], orr[8 * g + 1]), pack_bf16(orr[8 * g + 2], orr[8 * g + 3]),
+                         pack_bf16(orr[8 * g + 4], orr[8 * g + 5]), pack_bf16(orr[8 * g + 6], orr[8 * g + 7]));
+          *reinterpret_cast<uint4*>(sDp + tc::cm_offset_mn(m0, 128 + j2, 256)) =
+              make_uint4(pack_bf16(oi[8 * g], oi[8 * g + 1]), pack_bf16(oi[8 * g + 2], oi[8 * g + 3]),
+                         pack_bf16(oi[8 * g + 4], oi[8 * g + 5]), pack_bf16(oi[8 * g + 6], oi[8 * g + 7]));
         }
       }
     }
@@ -303,7 +320,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc::fence_after_sync();
     // ---- GEMM B: Re Y [tmem 256..383], Im Y [384..511] ----
     if (tid == 0) {
-      const uint32_t id = tc::make_idesc_bf16(128, 128), idn = tc::make_idesc_bf16(128, 128, true);
+      const uint32_t id = tc::make_idesc_bf16(128, 128, false, false, true),
+                     idn = tc::make_idesc_bf16(128, 128, true, false, true);   // D' is M-major
       const uint32_t tRe = tbase + 256u, tIm = tbase + 384u;
 #pragma unroll
       for (int s = 0; s < 8; ++s) {   // Re D' * Gr, Re D' * Gi
@@ -359,23 +377,22 @@ cudaError_t launch_rows_forward_tc(const RowCfg& c, const RowDev<float>* rows, i
   const unsigned grid = (unsigned)std::min<int64_t>(pairs, (int64_t)std::max(sms, 1));
   const uint4* A = static_cast<const uint4*>(c.tcA);
   const uint4* G = static_cast<const uint4*>(c.tcG);
-  const float2* tw = static_cast<const float2*>(c.tcTw);
   cudaError_t e;
   switch (env) {
     case ENV_BF16:
       if ((e = allow_smem((const void*)k_rows_forward_tc<ENV_BF16>, kTcSmem)) != cudaSuccess) return e;
       k_rows_forward_tc<ENV_BF16><<<grid, kTcThreads, kTcSmem, st>>>(
-          rows, n_rows, Nr, X, static_cast<__nv_bfloat162*>(y), units, A, G, tw, wtab);
+          rows, n_rows, Nr, X, static_cast<__nv_bfloat162*>(y), units, A, G, wtab);
       break;
     case ENV_F16:
       if ((e = allow_smem((const void*)k_rows_forward_tc<ENV_F16>, kTcSmem)) != cudaSuccess) return e;
       k_rows_forward_tc<ENV_F16><<<grid, kTcThreads, kTcSmem, st>>>(rows, n_rows, Nr, X, static_cast<__half2*>(y),
-                                                                    units, A, G, tw, wtab);
+                                                                    units, A, G, wtab);
       break;
     default:
       if ((e = allow_smem((const void*)k_rows_forward_tc<ENV_F32>, kTcSmem)) != cudaSuccess) return e;
       k_rows_forward_tc<ENV_F32><<<grid, kTcThreads, kTcSmem, st>>>(rows, n_rows, Nr, X, static_cast<float2*>(y),
-                                                                    units, A, G, tw, wtab);
+                                                                    units, A, G, wtab);
   }
   return cudaGetLastError();
 }
@@ -390,8 +407,8 @@ qtam_status qtam_tc_gemm_check(const void* A, const void* B, float* D, int32_t N
     qtam::set_last_error("NULL buffer");
     return QTAM_ERR_INVALID_ARG;
   }
-  if (N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16 || (flags & ~3)) {
-    qtam::set_last_error("N and K must be multiples of 16 in [16, 256]; flags in {0..3}");
+  if (N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16 || (flags & ~7)) {
+    qtam::set_last_error("N and K must be multiples of 16 in [16, 256]; flags in {0..7}");
     return QTAM_ERR_INVALID_ARG;
   }
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) {

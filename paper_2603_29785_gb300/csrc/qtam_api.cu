@@ -198,7 +198,6 @@ struct qtam_plan_s {
   void* d_wtab = nullptr;   // W'(0..h) per distinct half-width, non-bisquare windows only
   void* d_tcA = nullptr;    // tensor-core short DFT operands and twiddles (short_dft = TENSOR)
   void* d_tcG = nullptr;
-  void* d_tcTw = nullptr;
   size_t device_bytes = 0;
   std::map<int, void*> variant_tw;   // stage twiddle tables per row-kernel variant
   void* d_stw_col = nullptr;
@@ -374,21 +373,21 @@ uint16_t to_bf16(double x) {
   return (uint16_t)(b >> 16);
 }
 
-// Operands of the tensor-core four-step (M = 64 x 128), FP64-evaluated and
-// rounded once, in the K-major core-matrix layout of the MMA operands:
-//  A: DFT-64 block matrix, row 2 n1 + {re, im}, column j1 (times Re Z) or
-//     64 + j1 (times Im Z): [cos, -sin; sin, cos] of 2 pi j1 n1 / 64;
-//  G: cosine then sine DFT-128 matrices [n2][j2] of 2 pi j2 n2 / 128;
-//  twiddles e^{+2 pi i j2 n1 / 8192}, [n1][j2] complex FP32.
+// Constant operands of the tensor-core four-step (M = 64 x 128),
+// FP64-evaluated and rounded once, in the K-major core-matrix layout:
+//  A: DFT-64 block matrix as GEMM A's B operand, row n1 (Re D) or 64 + n1
+//     (Im D), column j1 (times Re Z) or 64 + j1 (times Im Z):
+//     [cos, -sin; sin, cos] of 2 pi j1 n1 / 64;
+//  G: cosine then sine DFT-128 matrices [n2][j2] of 2 pi j2 n2 / 128.
 qtam_status upload_tc_tables(qtam_plan_s* pl, size_t& tot) {
   const double two_pi = 6.283185307179586476925286766559;
   std::vector<uint16_t> A(128 * 128), G(2 * 128 * 128);
-  for (int m = 0; m < 128; ++m)
+  for (int c = 0; c < 128; ++c)
     for (int k = 0; k < 128; ++k) {
-      const int n1 = m >> 1, part = m & 1, j1 = k & 63, comp = k >> 6;
+      const int n1 = c & 63, part = c >> 6, j1 = k & 63, comp = k >> 6;
       const double th = two_pi * (double)((j1 * n1) % 64) / 64.0;
       const double v = part == 0 ? (comp == 0 ? std::cos(th) : -std::sin(th)) : (comp == 0 ? std::sin(th) : std::cos(th));
-      A[qtam::tc::cm_offset(m, k, 128) / 2] = to_bf16(v);
+      A[qtam::tc::cm_offset(c, k, 128) / 2] = to_bf16(v);
     }
   for (int n2 = 0; n2 < 128; ++n2)
     for (int j2 = 0; j2 < 128; ++j2) {
@@ -396,20 +395,11 @@ qtam_status upload_tc_tables(qtam_plan_s* pl, size_t& tot) {
       G[qtam::tc::cm_offset(n2, j2, 128) / 2] = to_bf16(std::cos(th));
       G[128 * 128 + qtam::tc::cm_offset(n2, j2, 128) / 2] = to_bf16(std::sin(th));
     }
-  std::vector<float> tw(2 * 64 * 128);
-  for (int n1 = 0; n1 < 64; ++n1)
-    for (int j2 = 0; j2 < 128; ++j2) {
-      const double th = two_pi * (double)((j2 * n1) % 8192) / 8192.0;
-      tw[2 * (n1 * 128 + j2)] = (float)std::cos(th);
-      tw[2 * (n1 * 128 + j2) + 1] = (float)std::sin(th);
-    }
   qtam_status s;
   if ((s = upload(&pl->d_tcA, A.data(), A.size() * 2, tot)) != QTAM_OK) return s;
   if ((s = upload(&pl->d_tcG, G.data(), G.size() * 2, tot)) != QTAM_OK) return s;
-  if ((s = upload(&pl->d_tcTw, tw.data(), tw.size() * sizeof(float), tot)) != QTAM_OK) return s;
   pl->rc.tcA = pl->d_tcA;
   pl->rc.tcG = pl->d_tcG;
-  pl->rc.tcTw = pl->d_tcTw;
   return QTAM_OK;
 }
 
@@ -507,7 +497,6 @@ void free_plan(qtam_plan_s* pl) {
     cudaFree(pl->d_wtab);
     cudaFree(pl->d_tcA);
     cudaFree(pl->d_tcG);
-    cudaFree(pl->d_tcTw);
     cudaFree(pl->d_stw_col);
     cudaFree(pl->d_stw_row);
     for (auto& kv : pl->variant_tw) cudaFree(kv.second);

@@ -53,12 +53,11 @@ struct RowCfg {
   size_t smem;
   int variant;   // index of a compile-time row-kernel variant, -1 = runtime engine
   const void* stw = nullptr;   // stage twiddle tables of that variant
-  // tensor-core short DFT (M = 8192): DFT-64 block operand, DFT-128 cosine and
-  // sine operands, four-step twiddles; used when `tensor` is set
+  // tensor-core short DFT (M = 8192): DFT-64 block operand, DFT-128 cosine
+  // and sine operands; used when `tensor` is set
   int tensor = 0;
   const void* tcA = nullptr;
   const void* tcG = nullptr;
-  const void* tcTw = nullptr;
 };
 
 enum EnvKind { ENV_F32 = 0, ENV_F64 = 1, ENV_BF16 = 2, ENV_F16 = 3 };

@@ -29,6 +29,15 @@ __host__ __device__ __forceinline__ uint32_t cm_offset(int row, int k, int K) {
   return (uint32_t)(((row >> 3) * (K >> 3) + (k >> 3)) * 128 + (row & 7) * 16 + (k & 7) * 2);
 }
 
+// The MN-major layout: a core matrix holds 8 K-rows of 16 bytes, each 8
+// consecutive M (or N) elements; core matrices are placed as in the K-major
+// case (K-adjacent ones 128 bytes apart, 8-row M groups K/8 * 128 apart), so
+// the descriptor offsets are the same and only the instruction descriptor's
+// major bit differs.
+__host__ __device__ __forceinline__ uint32_t cm_offset_mn(int row, int k, int K) {
+  return (uint32_t)(((row >> 3) * (K >> 3) + (k >> 3)) * 128 + (k & 7) * 16 + (row & 7) * 2);
+}
+
 // Shared-memory matrix descriptor (tcgen05 format): start address, leading
 // and stride byte offsets (all >> 4), descriptor version 1 at bits 46-47,
 // base offset 0, no swizzling (layout type 0 at bits 61-63).
@@ -40,14 +49,16 @@ __device__ __forceinline__ uint64_t make_sdesc(uint32_t saddr, uint32_t lbo, uin
   return d;
 }
 
-// Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, both
-// operands K-major, optional negation of A or B, tile M x N.
-__host__ __device__ constexpr uint32_t make_idesc_bf16(int M, int N, bool neg_a = false, bool neg_b = false) {
+// Instruction descriptor of kind::f16 with BF16 A and B, FP32 D, B K-major,
+// A K-major or M-major, optional negation of A or B, tile M x N.
+__host__ __device__ constexpr uint32_t make_idesc_bf16(int M, int N, bool neg_a = false, bool neg_b = false,
+                                                     bool a_mn_major = false) {
   return (1u << 4)                      // D format: F32
          | (1u << 7)                    // A format: BF16
          | (1u << 10)                   // B format: BF16
          | ((neg_a ? 1u : 0u) << 13)    // negate A
          | ((neg_b ? 1u : 0u) << 14)    // negate B
+         | ((a_mn_major ? 1u : 0u) << 15)   // A stored M-major
          | ((uint32_t)(N >> 3) << 17)   // N / 8
          | ((uint32_t)(M >> 4) << 24);  // M / 16
 }

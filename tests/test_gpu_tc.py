@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 
 @pytest.mark.parametrize("N,K,flags", [(256, 128, 0), (128, 256, 0), (16, 16, 0), (256, 256, 1), (64, 48, 2),
-                                       (144, 128, 3)])
+                                       (144, 128, 3), (128, 256, 4), (256, 128, 5), (32, 32, 4)])
 def test_tc_gemm_matches_float64(N, K, flags):
     g = torch.Generator().manual_seed(N * 1000 + K * 10 + flags)
     A = torch.randn((128, K), generator=g).to(torch.bfloat16)
