@@ -41,6 +41,18 @@ documented choice; the same list is kept in the design notes):
       of x onto F_tau.
   C9  a plane mask selects the planes whose rows are synthesised and whose
       windows enter P.
+  D1  dense mode (Sec. III alternative inversion; App. A regularisation):
+      with stopband_eps > 0 every window is W' where W' > 0 and eps wherever
+      it vanishes (outside |d| <= h, and at the edge points |d| = h where the
+      printed window is exactly zero although the text wants it strictly
+      non-zero), so each tile spans all N/2 + 1 bins
+      (M >= N/2 + 1 for a lossless tile) and any single tile inverts by
+      spectral division, x = irfft( T~_k / W_k ) (the equation after
+      Eq. qtam_window_formula).  c_k keeps its value from the band.  With
+      remodulate the envelope is multiplied by exp(+2 pi i k_c n / M), the
+      carrier the demodulation removed: the tile is then the plain inverse
+      DFT of the unshifted filtered spectrum X W_k (the undemodulated,
+      "standard" tile, here on M columns).
   S1  streaming (the paper motivates hours-long signals, Sec. I, without
       fixing a scheme): overlap-save with chunks of the plan's length N, hop H
       and guard G = (N - H)/2 on each side; each chunk keeps its central
@@ -113,6 +125,8 @@ class Geometry:
     c: np.ndarray           # [P, K] window normalisation c_k
     window: object = "bisquare"       # one name, or one per plane (composite bank)
     window_param: object = 0.0        # one value, or one per plane
+    eps: float = 0.0                  # stopband floor of every window (reading D1)
+    remodulate: bool = False          # envelopes carry the carrier again (reading D1)
     extra: dict = field(default_factory=dict)
 
     def plane_window(self, p: int):
@@ -215,7 +229,8 @@ def window_norm(h: int, norm: str, window: str = "bisquare", param: float = 0.0)
 
 
 def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
-             max_window_hz=0.0, n_out=0, window="bisquare", window_param=0.0) -> Geometry:
+             max_window_hz=0.0, n_out=0, window="bisquare", window_param=0.0,
+             stopband_eps=0.0, remodulate=False) -> Geometry:
     """Plan the filter bank: grid, centre bins, half-widths, c_k and M.
 
     App. A (grid f_k, L_k^ideal proportional to f_k N_t / Q, automatic clamp
@@ -256,6 +271,10 @@ def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
             wpar = window_param if np.ndim(window_param) == 0 else window_param[p]
             c[p, k] = window_norm(int(h[p, k]), norm, wname, float(wpar))
     Lmax = int(np.max(2 * h + 1))
+    if stopband_eps < 0:
+        raise ValueError("stopband_eps must be >= 0")
+    if stopband_eps > 0:
+        Lmax = max(Lmax, N // 2 + 1)          # every tile spans the whole one-sided spectrum
     if n_out:
         if n_out < Lmax:
             raise ValueError("n_out shorter than the largest window: aliasing")
@@ -267,13 +286,32 @@ def geometry(fs, N, qs, fmin, fmax, K, norm="l2", q_width=math.sqrt(11.0),
                     h_max=int(h_max), M=M, f=f, kc=kc, h=h, c=c,
                     window=window if isinstance(window, str) else tuple(window),
                     window_param=float(window_param) if np.ndim(window_param) == 0
-                    else tuple(float(a) for a in window_param))
+                    else tuple(float(a) for a in window_param),
+                    eps=float(stopband_eps), remodulate=bool(remodulate))
+
+
+def row_weight(g: Geometry, p: int, k: int, d: np.ndarray) -> np.ndarray:
+    """c_k W_k at offsets d from the centre: the window where it is positive
+    and the stopband floor eps wherever it vanishes -- outside |d| <= h and at
+    the support's edge points, where the printed window is exactly zero
+    (reading D1; eps = 0 by default)."""
+    d = np.asarray(d, dtype=np.int64)
+    w = window_profile(d, int(g.h[p, k]), *g.plane_window(p))
+    if g.eps > 0:
+        w = np.where(w > 0, w, g.eps)
+    return g.c[p, k] * w
+
+
+def carrier(g: Geometry, p: int, k: int) -> np.ndarray:
+    """exp(+2 pi i k_c n / M), n = 0..M-1 (k_c n reduced mod M in integers)."""
+    n = np.arange(g.M, dtype=np.int64)
+    return np.exp(2j * np.pi * np.mod(int(g.kc[p, k]) * n, g.M) / g.M)
 
 
 def window(g: Geometry, p: int, k: int) -> np.ndarray:
     """Dense W_k[f], f = 0..N/2, truncated to the one-sided band (reading C6)."""
     fbin = np.arange(g.Nr)
-    return g.c[p, k] * window_profile(fbin - g.kc[p, k], int(g.h[p, k]), *g.plane_window(p))
+    return row_weight(g, p, k, fbin - g.kc[p, k])
 
 
 def frame_operator(g: Geometry, planes=None) -> np.ndarray:
@@ -300,8 +338,12 @@ def spectrum(x: np.ndarray) -> np.ndarray:
 
 
 def band(g: Geometry, p: int, k: int):
-    """Offsets d in [-h, h] whose bins k_c + d lie in 0..N/2, and those bins."""
+    """Offsets d in [-h, h] whose bins k_c + d lie in 0..N/2, and those bins
+    (every bin 0..N/2 in dense mode, reading D1)."""
     hk = int(g.h[p, k])
+    if g.eps > 0:
+        fb = np.arange(g.Nr)
+        return fb - g.kc[p, k], fb
     d = np.arange(-hk, hk + 1)
     fb = g.kc[p, k] + d
     ok = (fb >= 0) & (fb <= g.N // 2)
@@ -319,9 +361,9 @@ def forward_row(g: Geometry, X: np.ndarray, p: int, k: int) -> np.ndarray:
     """
     d, fb = band(g, p, k)
     Z = np.zeros(g.M, dtype=np.complex128)
-    w = g.c[p, k] * window_profile(d, int(g.h[p, k]), *g.plane_window(p))
-    Z[d % g.M] = w * X[fb]
-    return np.fft.ifft(Z) * math.sqrt(g.M / g.N)
+    Z[d % g.M] = row_weight(g, p, k, d) * X[fb]
+    Y = np.fft.ifft(Z) * math.sqrt(g.M / g.N)
+    return Y * carrier(g, p, k) if g.remodulate else Y
 
 
 def forward(g: Geometry, x: np.ndarray) -> np.ndarray:
@@ -345,10 +387,10 @@ def accumulate(g: Geometry, Y: np.ndarray, planes=None) -> np.ndarray:
     A = np.zeros(g.Nr, dtype=np.complex128)
     for p in planes:
         for k in range(g.K):
-            S = np.fft.fft(Y[p, k]) * math.sqrt(g.N / g.M)
+            y = Y[p, k] * np.conj(carrier(g, p, k)) if g.remodulate else Y[p, k]
+            S = np.fft.fft(y) * math.sqrt(g.N / g.M)
             d, fb = band(g, p, k)
-            w = g.c[p, k] * window_profile(d, int(g.h[p, k]), *g.plane_window(p))
-            A[fb] += w * S[d % g.M]
+            A[fb] += row_weight(g, p, k, d) * S[d % g.M]
     return A
 
 
@@ -370,6 +412,21 @@ def inverse(g: Geometry, Y: np.ndarray, planes=None, tau: float = 0.0) -> np.nda
     keep = kept_bins(Pf, tau)
     Xh = np.zeros(g.Nr, dtype=np.complex128)
     Xh[keep] = A[keep] / Pf[keep]
+    return real_ifft(Xh, g.N)
+
+
+def inverse_single_tile(g: Geometry, Y: np.ndarray, p: int, k: int) -> np.ndarray:
+    """Reconstruction from the one tile (p, k) by spectral division (the
+    equation after Eq. qtam_window_formula): the tile spectrum shifted back to
+    its carrier, T~_k[f] = sqrt(N/M) FFT_M(Y_k)[f - k_c], divided by c_k W_k[f]
+    on every bin; needs the dense mode (eps > 0, M >= N/2 + 1)."""
+    if g.eps <= 0 or g.M < g.Nr:
+        raise ValueError("the single-tile inverse needs stopband_eps > 0 and M >= N/2 + 1")
+    y = Y[p, k] * np.conj(carrier(g, p, k)) if g.remodulate else Y[p, k]
+    S = np.fft.fft(y) * math.sqrt(g.N / g.M)
+    d, fb = band(g, p, k)
+    Xh = np.zeros(g.Nr, dtype=np.complex128)
+    Xh[fb] = S[d % g.M] / row_weight(g, p, k, d)
     return real_ifft(Xh, g.N)
 
 

@@ -22,6 +22,8 @@ PIN_TESTS = [
     lambda gd: pins.test_grid_and_widths_follow_formulas(),
     lambda gd: pins.test_stream_of_a_periodic_signal_tiles_the_circular_transform(),
     lambda gd: pins.test_stream_layout_rules(),
+    lambda gd: pins.test_remodulated_tile_is_the_unshifted_filtered_spectrum(),
+    lambda gd: pins.test_single_tile_inverse_recovers_the_signal(True),
 ]
 
 
@@ -68,6 +70,13 @@ def _acc_conj(g, Y, planes=None):
     return _orig_acc(g, np.conj(Y), planes)
 
 
+_orig_carrier = O.carrier
+
+
+def _carrier_conj(g, p, k):
+    return np.conj(_orig_carrier(g, p, k))
+
+
 _orig_phase = O.stream_phase
 _orig_layout = O.stream_layout
 
@@ -91,6 +100,7 @@ MUTANTS = {
     "synthesis of conj(Y)": ("accumulate", _acc_conj),
     "stream phase conjugated": ("stream_phase", _phase_wrong_sign),
     "stream crop one column late": ("stream_layout", _layout_crop_off_by_one),
+    "remodulation with the conjugate carrier": ("carrier", _carrier_conj),
 }
 
 

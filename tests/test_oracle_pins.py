@@ -499,3 +499,63 @@ def test_stream_without_guard_is_chunkwise():
         assert np.array_equal(Ymap[:, :, i * g.M:(i + 1) * g.M], Yi)
         assert np.allclose(O.stream_inverse(g, Ymap, g.N)[i * g.N:(i + 1) * g.N], O.inverse(g, Yi), rtol=0,
                            atol=1e-13 * np.max(np.abs(x)))
+
+
+# --------------------------------------------------------------------------- dense mode (reading D1)
+def _dense_geom(eps=1e-6, remodulate=False, **kw):
+    # N = 512: N/2 + 1 = 257 bins, M = 270 (smallest 2^a 3^b 5^c >= 257)
+    return O.geometry(64.0, 512, (4.0, 8.0), 3.0, 30.0, 12, stopband_eps=eps, remodulate=remodulate, **kw)
+
+
+def test_dense_geometry_spans_the_spectrum():
+    g = _dense_geom()
+    assert g.M == 270 and g.M >= g.Nr
+    d, fb = O.band(g, 0, 3)
+    assert np.array_equal(fb, np.arange(g.Nr))
+    w = O.row_weight(g, 0, 3, d)
+    hk = int(g.h[0, 3])
+    assert np.all(w[np.abs(d) >= hk] == g.c[0, 3] * 1e-6) and np.all(w > 0)     # edge points too
+    assert np.allclose(w[np.abs(d) < hk], g.c[0, 3] * O.bisquare_profile(d[np.abs(d) < hk], hk), rtol=1e-15)
+    assert np.array_equal(g.c, O.geometry(64.0, 512, (4.0, 8.0), 3.0, 30.0, 12, n_out=270).c)
+    with pytest.raises(ValueError):
+        O.geometry(64.0, 512, (4.0, 8.0), 3.0, 30.0, 12, stopband_eps=1e-6, n_out=256)
+
+
+@pytest.mark.parametrize("remodulate", [False, True])
+def test_single_tile_inverse_recovers_the_signal(remodulate):
+    """With a non-zero stopband every tile is element-wise invertible: each
+    single tile gives back x (the equation after Eq. qtam_window_formula)."""
+    g = _dense_geom(remodulate=remodulate)
+    x = _rand_x(g.N, 61)
+    Y = O.forward(g, x)
+    for p, k in ((0, 0), (0, 6), (1, 11), (1, 4)):
+        assert np.linalg.norm(O.inverse_single_tile(g, Y, p, k) - x) < 1e-8 * np.linalg.norm(x)
+    # the frame inverse is exact too (P > 0 on every bin); bins that only the
+    # floor covers have P ~ (c eps)^2, which lifts FP64 rounding by ~1/eps
+    assert np.linalg.norm(O.inverse(g, Y) - x) < 1e-9 * np.linalg.norm(x)
+    with pytest.raises(ValueError):
+        O.inverse_single_tile(small_geom(), O.forward(small_geom(), x), 0, 0)
+
+
+def test_remodulated_tile_is_the_unshifted_filtered_spectrum():
+    """T_k = Y_k exp(+2 pi i k_c n / M) is sqrt(M/N) IDFT_M of X W_k placed at
+    the absolute bins f (no roll): the undemodulated tile."""
+    g = _dense_geom(remodulate=True)
+    x = _rand_x(g.N, 62)
+    X = np.fft.rfft(x)
+    Y = O.forward(g, x)
+    for p, k in ((0, 2), (1, 9)):
+        V = np.zeros(g.M, dtype=np.complex128)
+        V[:g.Nr] = O.window(g, p, k) * X
+        assert np.allclose(np.fft.fft(Y[p, k]) / np.sqrt(g.M / g.N), V, rtol=0, atol=1e-12 * np.max(np.abs(V)))
+
+
+def test_small_stopband_barely_changes_the_tile():
+    """eps of the order of the working precision leaves the forward transform
+    as it was (Sec. III: negligible impact): the change is bounded by eps."""
+    g0 = O.geometry(64.0, 512, (4.0, 8.0), 3.0, 30.0, 12, n_out=270)
+    g1 = _dense_geom(eps=1e-9)
+    x = _rand_x(g0.N, 63)
+    Y0, Y1 = O.forward(g0, x), O.forward(g1, x)
+    assert np.linalg.norm(Y1 - Y0) <= 1e-9 * np.max(g1.c) * np.linalg.norm(np.fft.rfft(x)) * np.sqrt(g1.P * g1.K)
+    assert np.linalg.norm(Y1 - Y0) > 0
