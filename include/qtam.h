@@ -114,6 +114,19 @@ typedef struct {
    * QTAM_ERR_UNSUPPORTED_SIZE).  Its envelopes carry BF16 operand rounding
    * (relative error ~1e-3); the inverse stays on the CUDA cores. */
   int32_t short_dft;
+  /* dense mode (NEXT to the demodulated default; Sec. III alternative
+   * inversion): stopband_eps > 0 gives every window the floor eps wherever it
+   * vanishes (outside the support and at its edge points), so each tile
+   * spans all N/2+1 bins; n_out (M) must then be >= N/2+1 (default: the
+   * smallest 2^a 3^b 5^c above it) and any single tile inverts by spectral
+   * division (qtam_inverse_single_tile).  remodulate = 1 multiplies the
+   * envelopes by exp(+2 pi i k_c n / M): the undemodulated tile, i.e. the
+   * inverse DFT of the unshifted filtered spectrum X W_k.  Both run the
+   * CUDA-core runtime engine (no compile-time variants, no tensor cores);
+   * remodulate combined with short_dft = TENSOR, or eps with it, is
+   * QTAM_ERR_UNSUPPORTED_SIZE. */
+  double stopband_eps;
+  int32_t remodulate;
 } qtam_plan_desc;
 
 typedef struct {
@@ -204,6 +217,15 @@ QTAM_API qtam_status qtam_stage_accumulate(qtam_plan_t plan, const void* y, int6
                                   void* A, void* stream);
 QTAM_API qtam_status qtam_stage_synthesize(qtam_plan_t plan, const void* A, int64_t batch, uint64_t plane_mask,
                                   void* x, void* workspace, size_t workspace_bytes, void* stream);
+
+/* Single-tile inverse of the dense mode: x[b] = irfft( T~_k / W_k ) from the
+ * one tile (plane, row) of y [batch][P][K][M] -- the tile's spectrum shifted
+ * back to its carrier and divided by its (floored) window on every bin.
+ * Needs stopband_eps > 0 (else QTAM_ERR_INVALID_ARG); other tiles are not
+ * read.  Workspace as for qtam_inverse. */
+QTAM_API qtam_status qtam_inverse_single_tile(qtam_plan_t plan, const void* y, int64_t batch, int32_t plane,
+                                              int32_t row, void* x, void* workspace, size_t workspace_bytes,
+                                              void* stream);
 
 /* Forward then inverse from HOST buffers: copies x_host into x_dev, runs
  * qtam_forward into y_dev and qtam_inverse into xhat_dev, and copies xhat_dev

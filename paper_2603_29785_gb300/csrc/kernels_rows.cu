@@ -90,6 +90,7 @@ template <typename T, bool FEXACT> struct RowCtx {
   T kw, h2;
   const T* wt;   // runtime engine only: W'(0..h) table of a non-bisquare window, or null
   T cw;          // its normalisation (c_fwd or c_inv)
+  T ew;          // runtime engine only: weight where the window vanishes (dense mode), else 0
   __device__ __forceinline__ void locate(int i, bool& in, int& d) const {
     const bool lo = i <= dhi;
     in = lo || i >= mlo;
@@ -102,7 +103,8 @@ template <typename T, bool FEXACT> struct RowCtx {
       u = (h2 - df * df) * kw;
     } else {
       const int a = d < 0 ? -d : d;
-      if (wt) return cw * wt[a <= h ? a : h];
+      if (wt) return a <= h ? cw * wt[a] : ew;
+      if (a >= h) return ew;
       u = (T)(h - a) * (T)(h + a) * kw;
     }
     return u * u;
@@ -152,6 +154,41 @@ template <typename V, int E> struct LoadEnvelope {
   }
 };
 
+// e^{sign 2 pi i (kc i mod M) / M}, the integer product reduced first
+template <typename V>
+__device__ __forceinline__ V carrier_rot(V v, int kc, int i, int M, bool conj) {
+  using T = decltype(v.x);
+  const int m = (int)(((long long)kc * i) % M);
+  T s, c;
+  if constexpr (sizeof(T) == 4) {
+    sincospif(2.0f * (float)m / (float)M, &s, &c);
+  } else {
+    sincospi(2.0 * (double)m / (double)M, &s, &c);
+  }
+  if (conj) s = -s;
+  return mk<V>(v.x * c - v.y * s, v.x * s + v.y * c);
+}
+
+// runtime-engine envelope store / load with the optional carrier (dense mode)
+template <typename V, int E> struct StoreEnvelopeRT {
+  typename Env<V, E>::S* ys;
+  bool valid;
+  int remod, kc, M;
+  __device__ __forceinline__ void put(int, int i, V v) const {
+    if (remod) v = carrier_rot(v, kc, i, M, false);
+    if (valid) stream_store(&ys[i], Env<V, E>::to(v));
+  }
+};
+template <typename V, int E> struct LoadEnvelopeRT {
+  const typename Env<V, E>::S* ys;
+  bool valid;
+  int remod, kc, M;
+  __device__ __forceinline__ V get(int, int i) const {
+    V v = valid ? Env<V, E>::from(stream_load(&ys[i])) : mk<V>(0, 0);
+    return remod ? carrier_rot(v, kc, i, M, true) : v;
+  }
+};
+
 // *p += v when `on` (relaxed, device scope); the float2 form is one
 // predicated vector reduction, so out-of-band positions cost no branch (the
 // accumulator is not read in the same kernel: no ordering with other accesses)
@@ -179,6 +216,27 @@ template <typename T, bool FEXACT, bool PRED> struct AccumulateBand {
     const T w = r.weight(d);
     if constexpr (PRED) {
       add_if(&As[r.kc + d], cscale(v, w), in);
+    } else if (in) {
+      add_if(&As[r.kc + d], cscale(v, w), true);
+    }
+  }
+};
+
+// runtime-engine inverse store: accumulate v * weight(d), or (single-tile
+// inverse) write v * scale / weight(d); in dense mode every bin is written once
+template <typename T> struct AccumulateBandRT {
+  using V = cplx<T>;
+  V* As;
+  RowCtx<T, false> r;
+  int divide;
+  T scale;
+  __device__ __forceinline__ void put(int, int i, V v) const {
+    bool in;
+    int d;
+    r.locate(i, in, d);
+    const T w = r.weight(d);
+    if (divide) {
+      if (in) As[r.kc + d] = cscale(v, scale / w);
     } else if (in) {
       add_if(&As[r.kc + d], cscale(v, w), true);
     }
@@ -223,6 +281,7 @@ __device__ __forceinline__ RowCtx<T, FEXACT> row_ctx(const RowDev<T>* rows, int 
   r.M = M;
   r.wt = nullptr;
   r.cw = (T)0;
+  r.ew = (T)0;
   if (valid) {
     const RowDev<T> rd = rows[row];
     const int nhalf = (int)(Nr - 1);
@@ -234,8 +293,9 @@ __device__ __forceinline__ RowCtx<T, FEXACT> row_ctx(const RowDev<T>* rows, int 
       r.wt = wtab + rd.woff;
       r.cw = inv ? rd.c_inv : rd.c_fwd;
     }
-    r.dhi = min(rd.h, nhalf - rd.kc);     // may be < 0: no non-negative offset
-    r.mlo = M + max(-rd.h, -rd.kc);       // may be > M - 1: no negative offset
+    r.ew = inv ? rd.eps_inv : rd.eps_fwd;
+    r.dhi = min(rd.hb, nhalf - rd.kc);    // may be < 0: no non-negative offset
+    r.mlo = M + max(-rd.hb, -rd.kc);      // may be > M - 1: no negative offset
     if (r.dhi < -1) r.dhi = -1;
   } else {
     r.kc = 0; r.h = 1; r.kw = 0; r.h2 = 1;
@@ -283,19 +343,42 @@ __device__ __forceinline__ void rows_inverse_body(const Eng& eng, const RowDev<T
   eng.template run<-1>(sm, twM, ld, stv);
 }
 
+// The runtime-engine kernels carry the dense-mode options (carrier, division)
 template <typename T, int E>
 __global__ void __launch_bounds__(kMaxBlock, 1)
     k_rows_forward(GenericEngine eng, const RowDev<T>* __restrict__ rows, int n_rows, int64_t Nr,
                    const cplx<T>* __restrict__ X, typename Env<cplx<T>, E>::S* __restrict__ y, int64_t n_units,
-                   const cplx<T>* __restrict__ twM, const T* __restrict__ wtab) {
-  rows_forward_body<GenericEngine, T, E>(eng, rows, n_rows, Nr, X, y, n_units, twM, wtab);
+                   const cplx<T>* __restrict__ twM, const T* __restrict__ wtab, DenseArgs<T> da) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int M = eng.m();
+  const int64_t unit = blockIdx.x;
+  const bool valid = unit < n_units;
+  const int64_t seg = valid ? unit / n_rows : 0;
+  const int row = valid ? (int)(unit - seg * n_rows) : 0;
+  const RowCtx<T, false> rc = row_ctx<T, false>(rows, row, M, Nr, valid, false, wtab);
+  LoadBand<T, false> ld{X + seg * Nr, rc};
+  StoreEnvelopeRT<V, E> stv{y + (valid ? unit : 0) * M, valid, da.remod, rc.kc, M};
+  eng.template run<+1>(sm, twM, ld, stv);
 }
 template <typename T, int E>
 __global__ void __launch_bounds__(kMaxBlock, 1)
     k_rows_inverse(GenericEngine eng, const RowDev<T>* __restrict__ rows, const int* __restrict__ row_list, int n_sel,
                    int n_rows, int64_t Nr, const typename Env<cplx<T>, E>::S* __restrict__ y, cplx<T>* __restrict__ A,
-                   int64_t n_units, const cplx<T>* __restrict__ twM, const T* __restrict__ wtab) {
-  rows_inverse_body<GenericEngine, T, E>(eng, rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM, wtab);
+                   int64_t n_units, const cplx<T>* __restrict__ twM, const T* __restrict__ wtab, DenseArgs<T> da) {
+  using V = cplx<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  V* sm = reinterpret_cast<V*>(smraw);
+  const int M = eng.m();
+  const int64_t unit = blockIdx.x;
+  const bool valid = unit < n_units;
+  const int64_t seg = valid ? unit / n_sel : 0;
+  const int row = valid ? row_list[unit - seg * n_sel] : 0;
+  const RowCtx<T, false> rc = row_ctx<T, false>(rows, row, M, Nr, valid, true, wtab);
+  LoadEnvelopeRT<V, E> ld{y + (seg * n_rows + row) * M, valid, da.remod, rc.kc, M};
+  AccumulateBandRT<T> stv{A + seg * Nr, rc, da.divide, da.scale};
+  eng.template run<-1>(sm, twM, ld, stv);
 }
 
 template <class Eng, int E>
@@ -478,8 +561,10 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
                                 void* y, int env, int64_t B, const cplx<T>* twM, cudaStream_t st, const T* wtab) {
   const int64_t units = B * n_rows;
   if (units == 0) return cudaSuccess;
+  DenseArgs<T> da;
+  da.remod = c.remod;
   if constexpr (sizeof(T) == 4) {
-    if (const RowVariant* v = row_variant(c.variant))
+    if (const RowVariant* v = c.remod ? nullptr : row_variant(c.variant))
       return v->fwd[env](rows, n_rows, Nr, X, y, B, static_cast<const float2*>(c.stw), st);
   }
   GenericEngine eng{c.rp};
@@ -489,22 +574,22 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
       case ENV_BF16:
         allow_smem((const void*)k_rows_forward<T, ENV_BF16>, c.smem);
         k_rows_forward<T, ENV_BF16><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
-                                                                       static_cast<__nv_bfloat162*>(y), units, twM, wtab);
+                                                                       static_cast<__nv_bfloat162*>(y), units, twM, wtab, da);
         break;
       case ENV_F16:
         allow_smem((const void*)k_rows_forward<T, ENV_F16>, c.smem);
         k_rows_forward<T, ENV_F16><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
-                                                                      static_cast<__half2*>(y), units, twM, wtab);
+                                                                      static_cast<__half2*>(y), units, twM, wtab, da);
         break;
       default:
         allow_smem((const void*)k_rows_forward<T, ENV_F32>, c.smem);
         k_rows_forward<T, ENV_F32><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
-                                                                      static_cast<float2*>(y), units, twM, wtab);
+                                                                      static_cast<float2*>(y), units, twM, wtab, da);
     }
   } else {
     allow_smem((const void*)k_rows_forward<T, ENV_F64>, c.smem);
     k_rows_forward<T, ENV_F64><<<blocks, c.threads, c.smem, st>>>(eng, rows, n_rows, Nr, X,
-                                                                  static_cast<double2*>(y), units, twM, wtab);
+                                                                  static_cast<double2*>(y), units, twM, wtab, da);
   }
   return cudaGetLastError();
 }
@@ -512,11 +597,12 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
 template <typename T>
 cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const int* row_list, int n_sel, int n_rows,
                                 int64_t Nr, const void* y, int env, cplx<T>* A, int64_t B, const cplx<T>* twM,
-                                cudaStream_t st, const T* wtab) {
+                                cudaStream_t st, const T* wtab, DenseArgs<T> da) {
   const int64_t units = B * n_sel;
+  da.remod = c.remod;
   if (units == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (const RowVariant* v = row_variant(c.variant))
+    if (const RowVariant* v = (c.remod || da.divide) ? nullptr : row_variant(c.variant))
       return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, static_cast<const float2*>(c.stw), st);
   }
   GenericEngine eng{c.rp};
@@ -526,22 +612,22 @@ cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const in
       case ENV_BF16:
         allow_smem((const void*)k_rows_inverse<T, ENV_BF16>, c.smem);
         k_rows_inverse<T, ENV_BF16><<<blocks, c.threads, c.smem, st>>>(
-            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __nv_bfloat162*>(y), A, units, twM, wtab);
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __nv_bfloat162*>(y), A, units, twM, wtab, da);
         break;
       case ENV_F16:
         allow_smem((const void*)k_rows_inverse<T, ENV_F16>, c.smem);
         k_rows_inverse<T, ENV_F16><<<blocks, c.threads, c.smem, st>>>(
-            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __half2*>(y), A, units, twM, wtab);
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const __half2*>(y), A, units, twM, wtab, da);
         break;
       default:
         allow_smem((const void*)k_rows_inverse<T, ENV_F32>, c.smem);
         k_rows_inverse<T, ENV_F32><<<blocks, c.threads, c.smem, st>>>(
-            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, twM, wtab);
+            eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, twM, wtab, da);
     }
   } else {
     allow_smem((const void*)k_rows_inverse<T, ENV_F64>, c.smem);
     k_rows_inverse<T, ENV_F64><<<blocks, c.threads, c.smem, st>>>(
-        eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const double2*>(y), A, units, twM, wtab);
+        eng, rows, row_list, n_sel, n_rows, Nr, static_cast<const double2*>(y), A, units, twM, wtab, da);
   }
   return cudaGetLastError();
 }
@@ -552,9 +638,9 @@ template cudaError_t launch_rows_forward<double>(const RowCfg&, const RowDev<dou
                                                  void*, int, int64_t, const double2*, cudaStream_t, const double*);
 template cudaError_t launch_rows_inverse<float>(const RowCfg&, const RowDev<float>*, const int*, int, int, int64_t,
                                                 const void*, int, float2*, int64_t, const float2*, cudaStream_t,
-                                                const float*);
+                                                const float*, DenseArgs<float>);
 template cudaError_t launch_rows_inverse<double>(const RowCfg&, const RowDev<double>*, const int*, int, int, int64_t,
                                                  const void*, int, double2*, int64_t, const double2*, cudaStream_t,
-                                                 const double*);
+                                                 const double*, DenseArgs<double>);
 
 }  // namespace qtam

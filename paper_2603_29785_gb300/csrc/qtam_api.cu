@@ -174,6 +174,8 @@ struct qtam_plan_s {
   int compute = QTAM_DTYPE_F32;
   int env = QTAM_DTYPE_F32;
   int short_dft = QTAM_SHORT_DFT_CUDA;
+  double eps = 0;        // dense mode: stopband floor of every window
+  int remod = 0;         // dense mode: envelopes carry the carrier
   double tau = 0;
   // geometry
   int P = 0;
@@ -198,6 +200,7 @@ struct qtam_plan_s {
   void* d_wtab = nullptr;   // W'(0..h) per distinct half-width, non-bisquare windows only
   void* d_tcA = nullptr;    // tensor-core short DFT operands and twiddles (short_dft = TENSOR)
   void* d_tcG = nullptr;
+  void* d_ones = nullptr;   // dense mode: 1/P := 1 for the single-tile inverse
   size_t device_bytes = 0;
   std::map<int, void*> variant_tw;   // stage twiddle tables per row-kernel variant
   void* d_stw_col = nullptr;
@@ -212,6 +215,11 @@ struct qtam_plan_s {
   }
   uint64_t all_mask() const { return P >= 64 ? ~0ull : ((1ull << P) - 1); }
   double wprof(int64_t d, int64_t hk, int p) const { return window_profile(d, hk, window[p], window_param[p]); }
+  // the window with the dense mode's floor: eps wherever the window vanishes
+  double wdense(int64_t d, int64_t hk, int p) const {
+    const double w = wprof(d, hk, p);
+    return (eps > 0 && !(w > 0)) ? eps : w;
+  }
   bool all_bisquare() const {
     for (int w : window)
       if (w != QTAM_WIN_BISQUARE) return false;
@@ -282,10 +290,11 @@ qtam_status build_mask(qtam_plan_s* pl, uint64_t mask, MaskEntry** out) {
   std::vector<double> wmax(pl->Nr, 0.0);
   for (int r : rows) {
     const int64_t hk = pl->h[r], kc = pl->kc[r];
-    for (int64_t d = -hk; d <= hk; ++d) {
+    const int64_t lo = pl->eps > 0 ? -kc : -hk, hi = pl->eps > 0 ? pl->Nr - 1 - kc : hk;
+    for (int64_t d = lo; d <= hi; ++d) {
       const int64_t fb = kc + d;
       if (fb < 0 || fb >= pl->Nr) continue;
-      wmax[fb] = std::max(wmax[fb], pl->c[r] * pl->wprof(d, hk, r / pl->K));
+      wmax[fb] = std::max(wmax[fb], pl->c[r] * pl->wdense(d, hk, r / pl->K));
     }
   }
   for (int64_t f = 0; f < pl->Nr; ++f)
@@ -438,6 +447,13 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
     rows[r].kw_fwd = (T)(std::sqrt(pl->c[r] / sMN) / ((double)pl->h[r] * (double)pl->h[r]));
     rows[r].kw_inv = (T)(std::sqrt(pl->c[r] * sNM) / ((double)pl->h[r] * (double)pl->h[r]));
     rows[r].woff = -1;
+    rows[r].hb = pl->eps > 0 ? (int)pl->n : pl->h[r];
+    rows[r].eps_fwd = (T)(pl->eps > 0 ? pl->c[r] / sMN * pl->eps : 0.0);
+    rows[r].eps_inv = (T)(pl->eps > 0 ? pl->c[r] * sNM * pl->eps : 0.0);
+  }
+  if (pl->eps > 0) {
+    std::vector<T> ones(pl->Nr, (T)1);
+    if ((s = upload(&pl->d_ones, ones.data(), ones.size() * sizeof(T), tot)) != QTAM_OK) return s;
   }
   if (!pl->all_bisquare()) {
     // one W'(0..h) table per distinct (window, parameter, half-width), read by
@@ -452,7 +468,7 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
       if (it == off.end()) {
         if (tab.size() + hk + 1 > (size_t)INT32_MAX) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "window tables too large");
         it = off.emplace(key, (int)tab.size()).first;
-        for (int a = 0; a <= hk; ++a) tab.push_back((T)pl->wprof(a, hk, p));
+        for (int a = 0; a <= hk; ++a) tab.push_back((T)pl->wdense(a, hk, p));
       }
       rows[r].woff = it->second;
     }
@@ -497,6 +513,7 @@ void free_plan(qtam_plan_s* pl) {
     cudaFree(pl->d_wtab);
     cudaFree(pl->d_tcA);
     cudaFree(pl->d_tcG);
+    cudaFree(pl->d_ones);
     cudaFree(pl->d_stw_col);
     cudaFree(pl->d_stw_row);
     for (auto& kv : pl->variant_tw) cudaFree(kv.second);
@@ -648,6 +665,10 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   if (d->length > ((int64_t)1 << 27)) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "length above 2^27");
   if (d->short_dft != QTAM_SHORT_DFT_CUDA && d->short_dft != QTAM_SHORT_DFT_TENSOR)
     return fail(QTAM_ERR_INVALID_ARG, "unknown short_dft");
+  if (!std::isfinite(d->stopband_eps) || d->stopband_eps < 0 || (d->remodulate != 0 && d->remodulate != 1))
+    return fail(QTAM_ERR_INVALID_ARG, "stopband_eps must be finite and >= 0, remodulate 0 or 1");
+  if ((d->stopband_eps > 0 || d->remodulate) && d->short_dft == QTAM_SHORT_DFT_TENSOR)
+    return fail(QTAM_ERR_UNSUPPORTED_SIZE, "the dense mode runs on the CUDA-core runtime engine");
   if (d->short_dft == QTAM_SHORT_DFT_TENSOR && (d->compute_dtype != QTAM_DTYPE_F32 || d->n_out != 8192))
     return fail(QTAM_ERR_UNSUPPORTED_SIZE, "the tensor-core short DFT needs n_out = 8192 and F32 compute");
 
@@ -671,6 +692,8 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->compute = d->compute_dtype;
   pl->env = d->envelope_dtype;
   pl->short_dft = d->short_dft;
+  pl->eps = d->stopband_eps;
+  pl->remod = d->remodulate;
   pl->tau = d->p_floor_rel >= 0 ? d->p_floor_rel : (pl->compute == QTAM_DTYPE_F64 ? 0.0 : 1e-6);
   pl->P = d->n_q;
   pl->n = pl->N / 2;
@@ -718,6 +741,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
       }
     }
   }
+  if (pl->eps > 0) Lmax = std::max<int64_t>(Lmax, pl->Nr);   // every tile spans the one-sided spectrum
   pl->Lmax = (int)Lmax;
   if (d->n_out > 0) {
     if (d->n_out < Lmax) {
@@ -735,10 +759,11 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   for (int r = 0; r < R; ++r) {
     const int p = r / pl->K;
     const int64_t hk = pl->h[r], kcr = pl->kc[r];
-    for (int64_t dd = -hk; dd <= hk; ++dd) {
+    const int64_t lo = pl->eps > 0 ? -kcr : -hk, hi = pl->eps > 0 ? pl->Nr - 1 - kcr : hk;
+    for (int64_t dd = lo; dd <= hi; ++dd) {
       const int64_t fb = kcr + dd;
       if (fb < 0 || fb >= pl->Nr) continue;
-      const double w = pl->c[r] * pl->wprof(dd, hk, p);
+      const double w = pl->c[r] * pl->wdense(dd, hk, p);
       pl->Pplane[p][fb] += w * w;
       ++pl->band_bins;
     }
@@ -754,7 +779,9 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.smem = smem_for(pl->rc.rp, 0, pl->cplx_size());
   pl->rc.variant = -1;
   pl->rc.tensor = pl->short_dft == QTAM_SHORT_DFT_TENSOR && tc_forward_supported(pl->M);
-  if (!dbl && pl->all_bisquare()) {   // compile-time variants hard-code the bisquare
+  pl->rc.remod = pl->remod;
+  const bool dense = pl->eps > 0 || pl->remod;   // runtime engine only
+  if (!dbl && pl->all_bisquare() && !dense) {   // compile-time variants hard-code the bisquare
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) {
         pl->rc.variant = v;   // first registered variant for this length
@@ -840,7 +867,7 @@ qtam_status qtam_plan_variants(qtam_plan_t pl, int32_t* ids, int32_t capacity, i
     ++n;
   };
   push(-1);
-  if (pl->compute == QTAM_DTYPE_F32 && pl->all_bisquare())
+  if (pl->compute == QTAM_DTYPE_F32 && pl->all_bisquare() && !(pl->eps > 0 || pl->remod))
     for (int v = 0; v < row_variant_count(); ++v)
       if (row_variant(v)->M == pl->M) push(v);
   *count = n;
@@ -851,7 +878,7 @@ qtam_status qtam_plan_set_variant(qtam_plan_t pl, int32_t id) {
   if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
   if (id != -1) {
     const RowVariant* v = row_variant(id);
-    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || !pl->all_bisquare())
+    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || !pl->all_bisquare() || pl->eps > 0 || pl->remod)
       return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length, dtype or window");
   }
   if (id >= 0 && pl->device >= 0) {
@@ -994,6 +1021,52 @@ qtam_status qtam_inverse(qtam_plan_t pl, const void* y, int64_t B, uint64_t mask
   }
   if ((s = run_accumulate<float>(pl, y, B, me, rg.r0, st)) != QTAM_OK) return s;
   return run_synthesize<float>(pl, rg.r0, B, me, x, ws, st);
+}
+
+qtam_status qtam_inverse_single_tile(qtam_plan_t pl, const void* y, int64_t B, int32_t plane, int32_t row, void* x,
+                                     void* ws, size_t wsb, void* stream) {
+  qtam_status s = common_checks(pl, B);
+  if (s != QTAM_OK) return s;
+  if (!(pl->eps > 0) || pl->M < pl->Nr)
+    return fail(QTAM_ERR_INVALID_ARG, "the single-tile inverse needs the dense mode (stopband_eps > 0)");
+  if (plane < 0 || plane >= pl->P || row < 0 || row >= pl->K) return fail(QTAM_ERR_INVALID_ARG, "no such tile");
+  MaskEntry* me = nullptr;
+  if ((s = get_mask(pl, pl->all_mask(), &me)) != QTAM_OK || B == 0) return s;
+  if (!x || !y || !ws) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (wsb < ws_bytes(pl, B)) return fail(QTAM_ERR_WORKSPACE, "workspace too small");
+  if (!aligned(x, pl->cplx_size()) || !aligned(y, pl->env_size()) || !aligned(ws, 256))
+    return fail(QTAM_ERR_INVALID_ARG, "misaligned buffer");
+  DeviceGuard g(pl->device);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Regions rg = split_ws(pl, ws, B);
+  const int* one_row = me->rows + (plane * pl->K + row);   // the all-planes row list is 0 .. P K - 1
+  const double scale = (double)pl->N / (double)pl->M;
+  cudaError_t e;
+  if (pl->compute == QTAM_DTYPE_F64) {
+    DenseArgs<double> da;
+    da.divide = 1;
+    da.scale = scale;
+    e = launch_rows_inverse<double>(pl->rc, static_cast<const RowDev<double>*>(pl->d_rows), one_row, 1, pl->P * pl->K,
+                                    pl->Nr, y, pl->env, static_cast<double2*>(rg.r0), B,
+                                    static_cast<const double2*>(pl->d_twM), st, static_cast<const double*>(pl->d_wtab),
+                                    da);
+    if (e != cudaSuccess) return fail_cuda(e, "single-tile launch");
+    e = launch_synthesis<double>(pl->lc, static_cast<const double2*>(rg.r0), static_cast<const double*>(pl->d_ones),
+                                 static_cast<double2*>(rg.r1), static_cast<double2*>(rg.r0), static_cast<double2*>(x),
+                                 B, static_cast<const double2*>(pl->d_twn), static_cast<const double2*>(pl->d_twN), st);
+  } else {
+    DenseArgs<float> da;
+    da.divide = 1;
+    da.scale = (float)scale;
+    e = launch_rows_inverse<float>(pl->rc, static_cast<const RowDev<float>*>(pl->d_rows), one_row, 1, pl->P * pl->K,
+                                   pl->Nr, y, pl->env, static_cast<float2*>(rg.r0), B,
+                                   static_cast<const float2*>(pl->d_twM), st, static_cast<const float*>(pl->d_wtab), da);
+    if (e != cudaSuccess) return fail_cuda(e, "single-tile launch");
+    e = launch_synthesis<float>(pl->lc, static_cast<const float2*>(rg.r0), static_cast<const float*>(pl->d_ones),
+                                static_cast<float2*>(rg.r1), static_cast<float2*>(rg.r0), static_cast<float2*>(x), B,
+                                static_cast<const float2*>(pl->d_twn), static_cast<const float2*>(pl->d_twN), st);
+  }
+  return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "synthesis launch");
 }
 
 qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, uint64_t mask, void* xhat_host,

@@ -31,6 +31,19 @@ template <typename T> struct RowDev {
   T kw_fwd;   // sqrt(c_fwd) / h^2: window weight c_fwd W'(d) = (kw_fwd (h^2 - d^2))^2
   T kw_inv;   // sqrt(c_inv) / h^2
   int woff;   // offset of this row's W'(0..h) in the plan's window table; -1: bisquare formula
+  int hb;     // half-width of the loaded band: h, or N/2 in dense mode (every bin)
+  T eps_fwd;  // dense mode: c_fwd eps, the weight wherever the window vanishes (else 0)
+  T eps_inv;  // dense mode: c_inv eps
+};
+
+// Runtime-engine options of the dense mode: remodulate multiplies the
+// envelopes by exp(+2 pi i k_c n / M) on store (and by its conjugate on load);
+// divide turns the inverse store into X[k_c + d] = v * scale / weight(d)
+// (the single-tile inverse) instead of accumulating v * weight(d).
+template <typename T> struct DenseArgs {
+  int remod = 0;
+  int divide = 0;
+  T scale = (T)0;
 };
 
 // Long real FFT of N = 2n samples as an n = n1 * n2 four-step complex FFT.
@@ -52,6 +65,7 @@ struct RowCfg {
   int threads;
   size_t smem;
   int variant;   // index of a compile-time row-kernel variant, -1 = runtime engine
+  int remod = 0; // dense mode: remodulated envelopes (runtime engine only)
   const void* stw = nullptr;   // stage twiddle tables of that variant
   // tensor-core short DFT (M = 8192): DFT-64 block operand, DFT-128 cosine
   // and sine operands; used when `tensor` is set
@@ -113,7 +127,7 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
 template <typename T>
 cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const int* row_list, int n_sel, int n_rows,
                                 int64_t Nr, const void* y, int env, cplx<T>* A, int64_t B, const cplx<T>* twM,
-                                cudaStream_t st, const T* wtab = nullptr);
+                                cudaStream_t st, const T* wtab = nullptr, DenseArgs<T> da = DenseArgs<T>());
 
 // radix sequence of the static long-FFT engine used for a pass of length m
 // with 2^nbs interleaved transforms (FP32); false when the runtime engine runs

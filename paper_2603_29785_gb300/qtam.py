@@ -48,6 +48,7 @@ class qtam_plan_desc(ctypes.Structure):
         ("compute_dtype", ctypes.c_int32), ("envelope_dtype", ctypes.c_int32), ("p_floor_rel", ctypes.c_double),
         ("window_param", ctypes.c_double), ("plane_window", ctypes.POINTER(ctypes.c_int32)),
         ("plane_window_param", ctypes.POINTER(ctypes.c_double)), ("short_dft", ctypes.c_int32),
+        ("stopband_eps", ctypes.c_double), ("remodulate", ctypes.c_int32),
     ]
 
 
@@ -100,6 +101,7 @@ SIGNATURES = {
     "qtam_stage_accumulate": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P]),
     "qtam_stage_synthesize": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P, _SZ, _P]),
     "qtam_roundtrip_host": (ctypes.c_int, [_P, _P, _I64, _U64, _P, _P, _P, _P, _P, _SZ, _P]),
+    "qtam_inverse_single_tile": (ctypes.c_int, [_P, _P, _I64, ctypes.c_int32, ctypes.c_int32, _P, _P, _SZ, _P]),
     "qtam_forward_noalloc": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
     "qtam_scale_rows": (ctypes.c_int, [_P, _P, _I64, _P, _P]),
     "qtam_plane_metrics": (ctypes.c_int, [_P, _P, _I64, _P, _P, _P]),
@@ -170,7 +172,7 @@ def _stream(stream) -> int | None:
 # ----------------------------------------------------------------------------
 def make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", q_width=0.0, max_window_hz=0.0,
               n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0, window="bisquare", window_param=0.0,
-              short_dft="cuda"):
+              short_dft="cuda", stopband_eps=0.0, remodulate=False):
     d = qtam_plan_desc()
     lib().qtam_plan_desc_init(ctypes.byref(d))
     qarr = (ctypes.c_double * len(qs))(*[float(q) for q in qs])
@@ -205,6 +207,8 @@ def make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", 
         if len(window_param) != len(qs):
             raise ValueError("one window parameter per plane is required")
     d.short_dft = SHORT_DFT[short_dft]
+    d.stopband_eps = float(stopband_eps)
+    d.remodulate = int(bool(remodulate))
     d._keep = keep
     return d
 
@@ -268,6 +272,11 @@ def qtam_forward(plan, x, batch, y, workspace, workspace_bytes, stream=None):
 def qtam_inverse(plan, y, batch, plane_mask, x, workspace, workspace_bytes, stream=None):
     _check(lib().qtam_inverse(plan, _ptr(y), int(batch), int(plane_mask), _ptr(x), _ptr(workspace),
                               int(workspace_bytes), _stream(stream)))
+
+
+def qtam_inverse_single_tile(plan, y, batch, plane, row, x, workspace, workspace_bytes, stream=None):
+    _check(lib().qtam_inverse_single_tile(plan, _ptr(y), int(batch), int(plane), int(row), _ptr(x), _ptr(workspace),
+                                          int(workspace_bytes), _stream(stream)))
 
 
 def qtam_stage_spectrum(plan, x, batch, X, workspace, workspace_bytes, stream=None):
@@ -420,12 +429,13 @@ class Plan:
 
     def __init__(self, sample_rate, length, qs, f_min, f_max, rows_per_plane, norm="l2", q_width=0.0,
                  max_window_hz=0.0, n_out=0, compute="f32", envelope=None, p_floor_rel=-1.0, device=0,
-                 window="bisquare", window_param=0.0, short_dft="cuda"):
+                 window="bisquare", window_param=0.0, short_dft="cuda", stopband_eps=0.0, remodulate=False):
         self.compute = compute
         self.envelope = envelope or compute
         self.device = int(device)
         self._desc = make_desc(sample_rate, length, qs, f_min, f_max, rows_per_plane, norm, q_width, max_window_hz,
-                               n_out, compute, self.envelope, p_floor_rel, window, window_param, short_dft)
+                               n_out, compute, self.envelope, p_floor_rel, window, window_param, short_dft,
+                               stopband_eps, remodulate)
         self.handle = qtam_plan(self._desc, self.device)
         self.info = qtam_plan_info(self.handle)
         self.N = self.info["length"]
@@ -515,6 +525,16 @@ class Plan:
             raise ValueError("x and y batch sizes differ")
         ws, wsb = self.workspace(B)
         qtam_inverse(self.handle, y, B, plane_mask, x, ws, wsb, stream)
+        return x
+
+    def inverse_single_tile(self, y, plane: int, row: int, x=None, stream=None):
+        """Dense mode: reconstruct every segment from its one tile (plane, row)."""
+        import torch
+        self._check_y(y)
+        B = y.shape[0]
+        x = torch.empty((B, self.N), dtype=self.real_dtype(), device=y.device) if x is None else self._check_x(x)
+        ws, wsb = self.workspace(B)
+        qtam_inverse_single_tile(self.handle, y, B, plane, row, x, ws, wsb, stream)
         return x
 
     def plane_metrics(self, y, stream=None):

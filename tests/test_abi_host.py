@@ -50,12 +50,17 @@ CASES = [
     # composite bank: planes scan Q x window x parameter
     dict(fs=4096, N=32768, qs=(8, 8, 8, 16, 16), fmin=20, fmax=2048, K=128,
          window=("bisquare", "tukey", "kaiser", "planck", "hann"), window_param=(0.0, 0.5, 6.0, 0.3, 0.0)),
+    # dense mode: stopband floor, tiles spanning the one-sided spectrum
+    dict(fs=64.0, N=512, qs=(4.0, 8.0), fmin=3.0, fmax=30.0, K=12, stopband_eps=1e-6),
+    dict(fs=4096, N=8192, qs=(4, 8, 16), fmin=20, fmax=2048, K=64, stopband_eps=1e-5, remodulate=True,
+         window="hann"),
 ]
 
 
 def _both(c):
     kw = dict(norm=c.get("norm", "l2"), max_window_hz=c.get("max_window_hz", 0.0), n_out=c.get("n_out", 0),
-              window=c.get("window", "bisquare"), window_param=c.get("window_param", 0.0))
+              window=c.get("window", "bisquare"), window_param=c.get("window_param", 0.0),
+              stopband_eps=c.get("stopband_eps", 0.0), remodulate=c.get("remodulate", False))
     g = O.geometry(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], **kw)
     p = qtam.Plan(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], device=-1, **kw)
     return g, p
@@ -64,7 +69,9 @@ def _both(c):
 @pytest.mark.parametrize("i", range(len(CASES)))
 def test_geometry_matches_oracle(i):
     g, p = _both(CASES[i])
-    assert p.M == g.M and p.info["max_window"] == int(g.L.max())
+    assert p.M == g.M
+    # the largest tile support: 2h + 1, or the whole one-sided spectrum in dense mode
+    assert p.info["max_window"] == (max(int(g.L.max()), g.Nr) if g.eps > 0 else int(g.L.max()))
     assert p.info["h_max"] == min(g.h_max, 2**31 - 1)
     assert np.array_equal(p.geometry.kc, g.kc)
     assert np.array_equal(p.geometry.h, g.h)
@@ -163,6 +170,22 @@ def test_tensor_short_dft_options():
     d = qtam.make_desc(*base)
     d.short_dft = 5
     assert _err(lambda: qtam.qtam_plan(d, -1)) == 1
+
+
+def test_dense_mode_options():
+    base = (4096.0, 8192, (8.0,), 20.0, 2048.0, 32)
+    p = qtam.Plan(*base, stopband_eps=1e-6, p_floor_rel=0.0, device=-1)
+    assert p.M == 4320 and p.info["max_window"] == 4097            # smallest 2^a 3^b 5^c >= N/2 + 1
+    assert p.info["kept_bins"] == 4097 and p.info["band_bins"] == 32 * 4097   # P > 0 on every bin
+    assert qtam.qtam_plan_variants(p.handle) == [-1]
+    assert _err(lambda: qtam.Plan(*base, stopband_eps=1e-6, n_out=4000, device=-1)) == 3    # aliasing
+    assert _err(lambda: qtam.Plan(*base, stopband_eps=-1.0, device=-1)) == 1
+    assert _err(lambda: qtam.Plan(*base, n_out=8192, stopband_eps=1e-6, short_dft="tensor", device=-1)) == 2
+    d = qtam.make_desc(*base)
+    d.remodulate = 2
+    assert _err(lambda: qtam.qtam_plan(d, -1)) == 1
+    q = qtam.Plan(*base, device=-1)
+    assert _err(lambda: qtam.qtam_inverse_single_tile(q.handle, 0, 1, 0, 0, 0, 0, 0, 0)) == 8   # host-only plan
 
 
 def test_f64_defaults():
