@@ -44,10 +44,11 @@ def parse():
     ap.add_argument("--cpu-sample-segments", type=int, default=4)
     ap.add_argument("--variant", type=int, default=None,
                     help="row-kernel variant id (default: chosen by the autotuner)")
-    ap.add_argument("--workload", default="64s", choices=["64s", "batched", "serving", "precision", "latency", "stream"],
+    ap.add_argument("--workload", default="64s", choices=["64s", "batched", "serving", "precision", "latency", "stream", "dense"],
                     help="64s: the headline workload (default); batched: 512 uneven segments in one graph; "
                          "serving: Poisson request stream; precision: envelope dtype sweep; "
-                         "stream: overlap-save over a continuous signal")
+                         "stream: overlap-save over a continuous signal; dense: stopband-floored tiles + "
+                         "single-tile inverse")
     ap.add_argument("--duration", type=float, default=60.0, help="seconds of arrivals for --workload serving")
     return ap.parse_args()
 
@@ -498,6 +499,62 @@ def run_stream(args, local):
     print(json.dumps(line), flush=True)
 
 
+def run_dense(args, local):
+    """Dense mode: 2 s @ 4096 Hz segments (N = 8192), Q {4,8,16} x 64 rows
+    20-2048 Hz, stopband floor eps = 1e-3, remodulated (undemodulated) tiles of
+    M = 4320 >= N/2 + 1 columns; forward of every tile, then the single-tile
+    inverse from one mid-band tile per segment (spectral division)."""
+    import torch
+    from oracle import qtam_oracle as O
+    from paper_2603_29785_gb300 import qtam, synth
+    torch.cuda.set_device(local)
+    fs, N, qs, K, eps = 4096.0, 8192, (4.0, 8.0, 16.0), 64, 1e-3
+    B = args.batch * 4
+    p = qtam.Plan(fs, N, qs, 20.0, 2048.0, K, stopband_eps=eps, remodulate=True, device=local)
+    xh_ = np.stack([synth.glitchy_segment(500 + b, N, fs, chirp=(b % 2 == 0)) for b in range(B)]).astype(np.float32)
+    x = torch.from_numpy(xh_).cuda()
+    y = p.forward(x)
+    xs = p.inverse_single_tile(y, 1, K // 2)
+    torch.cuda.synchronize()
+    g = O.geometry(fs, N, qs, 20.0, 2048.0, K, stopband_eps=eps, remodulate=True)
+    ef = max(float(np.linalg.norm(y[b].cpu().numpy() - O.forward(g, xh_[b].astype(np.float64)))
+                   / np.linalg.norm(O.forward(g, xh_[b].astype(np.float64)))) for b in range(2))
+    es = max(float(np.linalg.norm(xs[b].cpu().numpy() - xh_[b]) / np.linalg.norm(xh_[b])) for b in range(2))
+    st = torch.cuda.current_stream()
+    ws, wsb = p.workspace(B)
+    for _ in range(max(3, args.warmup)):
+        qtam.qtam_forward(p.handle, x, B, y, ws, wsb, st)
+        qtam.qtam_inverse_single_tile(p.handle, y, B, 1, K // 2, xs, ws, wsb, st)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+
+    def timed():
+        tf = ti = 0.0
+        for _ in range(args.steps):
+            ev[0].record(st)
+            qtam.qtam_forward(p.handle, x, B, y, ws, wsb, st)
+            ev[1].record(st)
+            qtam.qtam_inverse_single_tile(p.handle, y, B, 1, K // 2, xs, ws, wsb, st)
+            ev[2].record(st)
+            ev[2].synchronize()
+            tf += ev[0].elapsed_time(ev[1])
+            ti += ev[1].elapsed_time(ev[2])
+        return tf / args.steps, ti / args.steps
+    (ms_f, ms_i), clk = _clock_wrap(timed, local)
+    env_bytes = B * p.info["envelope_bytes_per_segment"]
+    line = {"metric": "QTAM dense mode: tiles Msamples/s and single-tile inverse Msamples/s",
+            "value": round(B * N / ms_f / 1e3, 2), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "ms_per_step": round(ms_f, 4), "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "2 s @ 4096 Hz segments, Q {4,8,16} x 64 rows 20-2048 Hz, stopband eps 1e-3, "
+                                   "remodulated tiles, M = %d" % p.M, "segments": B,
+                       "l2": "envelopes %.2f GB per step, larger than L2" % (env_bytes / 1e9)},
+            "forward_GB_s": round(env_bytes / (ms_f * 1e-3) / 1e9, 1),
+            "single_tile_inverse": {"value": round(B * N / ms_i / 1e3, 2), "ms_per_step": round(ms_i, 4),
+                                    "tile": [1, K // 2], "rel_err_vs_input": es},
+            "forward_rel_err_vs_oracle": ef, "clocks": clk}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args, local):
     """Poisson arrivals (200/s) of 3-channel 8 s @ 4096 Hz requests, Q in
     {8,16,32}, 20 % inverse of row-zeroed envelopes; 40 GB HBM budget."""
@@ -649,6 +706,8 @@ def main():
         return run_serving(args, local) if rank == 0 else None
     if args.workload == "precision":
         return run_precision(args, local) if rank == 0 else None
+    if args.workload == "dense":
+        return run_dense(args, local) if rank == 0 else None
     if args.workload == "stream":
         return run_stream(args, local) if rank == 0 else None
     if args.workload == "latency":

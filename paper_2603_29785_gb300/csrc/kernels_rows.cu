@@ -154,18 +154,12 @@ template <typename V, int E> struct LoadEnvelope {
   }
 };
 
-// e^{sign 2 pi i (kc i mod M) / M}, the integer product reduced first
+// v e^{+2 pi i (kcm i mod M) / M} (or its conjugate) from the plan's table
+// twM[t] = e^{-2 pi i t / M}; kcm = k_c mod M, so kcm i < M^2 fits 32 bits
 template <typename V>
-__device__ __forceinline__ V carrier_rot(V v, int kc, int i, int M, bool conj) {
-  using T = decltype(v.x);
-  const int m = (int)(((long long)kc * i) % M);
-  T s, c;
-  if constexpr (sizeof(T) == 4) {
-    sincospif(2.0f * (float)m / (float)M, &s, &c);
-  } else {
-    sincospi(2.0 * (double)m / (double)M, &s, &c);
-  }
-  if (conj) s = -s;
+__device__ __forceinline__ V carrier_rot(V v, const V* __restrict__ twM, int kcm, int i, int M, bool conj) {
+  const V w = twM[(int)((unsigned)(kcm * i) % (unsigned)M)];
+  const auto c = w.x, s = conj ? w.y : -w.y;
   return mk<V>(v.x * c - v.y * s, v.x * s + v.y * c);
 }
 
@@ -173,19 +167,21 @@ __device__ __forceinline__ V carrier_rot(V v, int kc, int i, int M, bool conj) {
 template <typename V, int E> struct StoreEnvelopeRT {
   typename Env<V, E>::S* ys;
   bool valid;
-  int remod, kc, M;
+  int remod, kcm, M;
+  const V* twM;
   __device__ __forceinline__ void put(int, int i, V v) const {
-    if (remod) v = carrier_rot(v, kc, i, M, false);
+    if (remod) v = carrier_rot(v, twM, kcm, i, M, false);
     if (valid) stream_store(&ys[i], Env<V, E>::to(v));
   }
 };
 template <typename V, int E> struct LoadEnvelopeRT {
   const typename Env<V, E>::S* ys;
   bool valid;
-  int remod, kc, M;
+  int remod, kcm, M;
+  const V* twM;
   __device__ __forceinline__ V get(int, int i) const {
     V v = valid ? Env<V, E>::from(stream_load(&ys[i])) : mk<V>(0, 0);
-    return remod ? carrier_rot(v, kc, i, M, true) : v;
+    return remod ? carrier_rot(v, twM, kcm, i, M, true) : v;
   }
 };
 
@@ -359,7 +355,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1)
   const int row = valid ? (int)(unit - seg * n_rows) : 0;
   const RowCtx<T, false> rc = row_ctx<T, false>(rows, row, M, Nr, valid, false, wtab);
   LoadBand<T, false> ld{X + seg * Nr, rc};
-  StoreEnvelopeRT<V, E> stv{y + (valid ? unit : 0) * M, valid, da.remod, rc.kc, M};
+  StoreEnvelopeRT<V, E> stv{y + (valid ? unit : 0) * M, valid, da.remod, rc.kc % M, M, twM};
   eng.template run<+1>(sm, twM, ld, stv);
 }
 template <typename T, int E>
@@ -376,7 +372,7 @@ __global__ void __launch_bounds__(kMaxBlock, 1)
   const int64_t seg = valid ? unit / n_sel : 0;
   const int row = valid ? row_list[unit - seg * n_sel] : 0;
   const RowCtx<T, false> rc = row_ctx<T, false>(rows, row, M, Nr, valid, true, wtab);
-  LoadEnvelopeRT<V, E> ld{y + (seg * n_rows + row) * M, valid, da.remod, rc.kc, M};
+  LoadEnvelopeRT<V, E> ld{y + (seg * n_rows + row) * M, valid, da.remod, rc.kc % M, M, twM};
   AccumulateBandRT<T> stv{A + seg * Nr, rc, da.divide, da.scale};
   eng.template run<-1>(sm, twM, ld, stv);
 }
