@@ -44,11 +44,11 @@ def parse():
     ap.add_argument("--cpu-sample-segments", type=int, default=4)
     ap.add_argument("--variant", type=int, default=None,
                     help="row-kernel variant id (default: chosen by the autotuner)")
-    ap.add_argument("--workload", default="64s", choices=["64s", "batched", "serving", "precision", "latency", "stream", "dense"],
+    ap.add_argument("--workload", default="64s", choices=["64s", "batched", "serving", "precision", "latency", "stream", "dense", "bank"],
                     help="64s: the headline workload (default); batched: 512 uneven segments in one graph; "
                          "serving: Poisson request stream; precision: envelope dtype sweep; "
                          "stream: overlap-save over a continuous signal; dense: stopband-floored tiles + "
-                         "single-tile inverse")
+                         "single-tile inverse; bank: Q x window composite bank with optimal-plane metrics")
     ap.add_argument("--duration", type=float, default=60.0, help="seconds of arrivals for --workload serving")
     return ap.parse_args()
 
@@ -555,6 +555,61 @@ def run_dense(args, local):
     print(json.dumps(line), flush=True)
 
 
+def run_bank(args, local):
+    """Composite bank (App. A): the 64 s workload with one App. A window per
+    plane -- (Q 4, bisquare), (8, Tukey 0.5), (16, Kaiser 8), (32, Hann),
+    (64, Planck-taper 0.3) -- forward + inverse, then the per-plane energy /
+    peak of every segment (optimal-plane selection), against the same
+    transform with the bisquare on every plane."""
+    import torch
+    from paper_2603_29785_gb300 import qtam, tune as qtune
+    torch.cuda.set_device(local)
+    W = WORKLOAD
+    B = args.batch
+    wins = ("bisquare", "tukey", "kaiser", "hann", "planck")
+    prms = (0.0, 0.5, 8.0, 0.0, 0.3)
+    x = torch.from_numpy(make_inputs(range(B))).cuda()
+    st = torch.cuda.current_stream()
+    out = {}
+    for label, kw in (("bank", dict(window=wins, window_param=prms)), ("bisquare", {})):
+        p = qtam.Plan(W["fs"], W["N"], W["qs"], W["fmin"], W["fmax"], W["K"], device=local, **kw)
+        qtune.tune(p, B)
+        y = p.forward(x)
+        xh = p.inverse(y)
+        energy = torch.empty((B, p.P), dtype=torch.float64, device=x.device)
+        peak = torch.empty((B, p.P), dtype=torch.float32, device=x.device)
+        ws, wsb = p.workspace(B)
+        for _ in range(max(3, args.warmup)):
+            qtam.qtam_forward(p.handle, x, B, y, ws, wsb, st)
+            qtam.qtam_inverse(p.handle, y, B, 0, xh, ws, wsb, st)
+            qtam.qtam_plane_metrics(p.handle, y, B, energy, peak, st)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(st)
+        for _ in range(args.steps):
+            qtam.qtam_forward(p.handle, x, B, y, ws, wsb, st)
+            qtam.qtam_inverse(p.handle, y, B, 0, xh, ws, wsb, st)
+        ev[1].record(st)
+        for _ in range(args.steps):
+            qtam.qtam_plane_metrics(p.handle, y, B, energy, peak, st)
+        ev[2].record(st)
+        ev[2].synchronize()
+        ms = ev[0].elapsed_time(ev[1]) / args.steps
+        ms_m = ev[1].elapsed_time(ev[2]) / args.steps
+        env_bytes = B * p.info["envelope_bytes_per_segment"]
+        out[label] = {"msamples_per_s": round(B * W["N"] / ms / 1e3, 1), "ms_per_step": round(ms, 4),
+                      "row_variant": qtam.qtam_variant_describe(p.info["row_variant"])["name"],
+                      "plane_metrics_ms": round(ms_m, 4),
+                      "plane_metrics_GB_s": round(env_bytes / (ms_m * 1e-3) / 1e9, 1),
+                      "best_plane_by_energy_seg0": int(torch.argmax(energy[0]).item())}
+    line = {"metric": "QTAM composite bank (Q x window) fwd+inv Msamples/s and optimal-plane metrics",
+            "value": out["bank"]["msamples_per_s"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": max(3, args.warmup), "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD_NAME + "; plane windows " + ", ".join(
+                f"{w}{'' if a == 0 else ' ' + str(a)}" for w, a in zip(wins, prms)), "segments": B},
+            "bank": out["bank"], "bisquare_all_planes": out["bisquare"]}
+    print(json.dumps(line), flush=True)
+
+
 def run_serving(args, local):
     """Poisson arrivals (200/s) of 3-channel 8 s @ 4096 Hz requests, Q in
     {8,16,32}, 20 % inverse of row-zeroed envelopes; 40 GB HBM budget."""
@@ -706,6 +761,8 @@ def main():
         return run_serving(args, local) if rank == 0 else None
     if args.workload == "precision":
         return run_precision(args, local) if rank == 0 else None
+    if args.workload == "bank":
+        return run_bank(args, local) if rank == 0 else None
     if args.workload == "dense":
         return run_dense(args, local) if rank == 0 else None
     if args.workload == "stream":

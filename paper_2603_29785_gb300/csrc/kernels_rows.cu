@@ -391,6 +391,28 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
   rows_inverse_body<Eng, float, E>(Eng(), rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM, nullptr);
 }
 
+// The same compile-time FFT with the weight read from the plan's window
+// table (the integer-product path of RowCtx): the bisquare kernels above keep
+// their exact-float formula and instruction stream untouched.
+template <class Eng> struct TabEngine : Eng {
+  static constexpr bool FEXACT = false;
+};
+template <class Eng, int E>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB)
+    k_rows_forward_st(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
+                      typename Env<float2, E>::S* __restrict__ y, int64_t n_units, const float2* __restrict__ twM,
+                      const float* __restrict__ wtab) {
+  rows_forward_body<TabEngine<Eng>, float, E>(TabEngine<Eng>(), rows, n_rows, Nr, X, y, n_units, twM, wtab);
+}
+template <class Eng, int E>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB)
+    k_rows_inverse_st(const RowDev<float>* __restrict__ rows, const int* __restrict__ row_list, int n_sel, int n_rows,
+                      int64_t Nr, const typename Env<float2, E>::S* __restrict__ y, float2* __restrict__ A,
+                      int64_t n_units, const float2* __restrict__ twM, const float* __restrict__ wtab) {
+  rows_inverse_body<TabEngine<Eng>, float, E>(TabEngine<Eng>(), rows, row_list, n_sel, n_rows, Nr, y, A, n_units, twM,
+                                              wtab);
+}
+
 // ---- registry of compile-time variants (FP32 compute) ------------------------
 template <class Eng, int E>
 cudaError_t fwd_launch(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
@@ -415,6 +437,30 @@ cudaError_t inv_launch(const RowDev<float>* rows, const int* row_list, int n_sel
   return cudaGetLastError();
 }
 
+template <class Eng>
+cudaError_t fwd_launch_tab(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
+                           const float2* twM, cudaStream_t st, const float* wtab) {
+  const int64_t units = B * n_rows;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_forward_st<Eng, ENV_F32>, smem);
+  k_rows_forward_st<Eng, ENV_F32><<<(unsigned)blocks, Eng::NT, smem, st>>>(rows, n_rows, Nr, X,
+                                                                            static_cast<float2*>(y), units, twM, wtab);
+  return cudaGetLastError();
+}
+template <class Eng>
+cudaError_t inv_launch_tab(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
+                           const void* y, float2* A, int64_t B, const float2* twM, cudaStream_t st,
+                           const float* wtab) {
+  const int64_t units = B * n_sel;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_inverse_st<Eng, ENV_F32>, smem);
+  k_rows_inverse_st<Eng, ENV_F32><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, twM, wtab);
+  return cudaGetLastError();
+}
+
 template <class Eng> RowVariant make_variant(const char* name) {
   RowVariant v;
   v.M = Eng::M;
@@ -432,37 +478,50 @@ template <class Eng> RowVariant make_variant(const char* name) {
   v.inv[ENV_F64] = nullptr;
   v.inv[ENV_BF16] = inv_launch<Eng, ENV_BF16>;
   v.inv[ENV_F16] = inv_launch<Eng, ENV_F16>;
+  v.fwd_tab = nullptr;
+  v.inv_tab = nullptr;
+  return v;
+}
+template <class Eng> RowVariant make_variant_tab(const char* name) {
+  RowVariant v = make_variant<Eng>(name);
+  v.fwd_tab = fwd_launch_tab<Eng>;
+  v.inv_tab = inv_launch_tab<Eng>;
   return v;
 }
 
 // StaticEngine<M, log2 rows per block, min blocks per SM, radices...>; the
 // first variant listed for a length is the default before tuning.
+// QTAM_VT: also built for window tables (the first such variant of a length
+// is the default of non-bisquare plans).
 #define QTAM_V(M, NBS, MINB, ...) \
   make_variant<StaticEngine<M, NBS, MINB, __VA_ARGS__>>(#M ":" #__VA_ARGS__ " rows/blk 2^" #NBS " minblk " #MINB)
+#define QTAM_VT(M, NBS, MINB, ...) \
+  make_variant_tab<StaticEngine<M, NBS, MINB, __VA_ARGS__>>(#M ":" #__VA_ARGS__ " rows/blk 2^" #NBS " minblk " #MINB)
 const RowVariant kVariants[] = {
-    QTAM_V(4800, 0, 4, 16, 20, 15),
+    QTAM_VT(4800, 0, 4, 16, 20, 15),
     QTAM_V(4800, 0, 3, 16, 20, 15),
     QTAM_V(4800, 0, 3, 16, 15, 20),
     QTAM_V(4800, 0, 2, 16, 20, 15),
     QTAM_V(4800, 0, 3, 8, 6, 10, 10),
     QTAM_V(4800, 0, 2, 16, 12, 25),
-    QTAM_V(2400, 0, 3, 16, 10, 15),
+    QTAM_VT(2400, 0, 3, 16, 10, 15),
     QTAM_V(2400, 1, 2, 16, 10, 15),
     QTAM_V(2400, 0, 4, 16, 10, 15),
-    QTAM_V(1200, 1, 2, 16, 15, 5),
+    QTAM_VT(1200, 1, 2, 16, 15, 5),
     QTAM_V(1200, 2, 2, 16, 3, 25),
-    QTAM_V(600, 3, 2, 8, 3, 25),
+    QTAM_VT(600, 3, 2, 8, 3, 25),
     QTAM_V(600, 2, 2, 8, 15, 5),
-    QTAM_V(500, 3, 2, 4, 5, 25),
-    QTAM_V(300, 3, 2, 12, 25),
+    QTAM_VT(500, 3, 2, 4, 5, 25),
+    QTAM_VT(300, 3, 2, 12, 25),
     QTAM_V(300, 4, 2, 4, 3, 25),
-    QTAM_V(150, 4, 2, 6, 25),
-    QTAM_V(75, 5, 2, 3, 25),
-    QTAM_V(8192, 0, 1, 16, 16, 32),
+    QTAM_VT(150, 4, 2, 6, 25),
+    QTAM_VT(75, 5, 2, 3, 25),
+    QTAM_VT(8192, 0, 1, 16, 16, 32),
     QTAM_V(8192, 0, 1, 32, 16, 16),
     QTAM_V(8192, 0, 1, 16, 32, 16),
 };
 #undef QTAM_V
+#undef QTAM_VT
 
 template <typename V, int E>
 __global__ void k_scale_rows(typename Env<V, E>::S* __restrict__ y, const float* __restrict__ gain, int64_t n_rows,
@@ -481,36 +540,63 @@ __global__ void k_scale_rows(typename Env<V, E>::S* __restrict__ y, const float*
   }
 }
 
-// Energy sum |Y|^2 and peak max |Y|^2 of one (segment, plane): a block per
-// pair, per-thread partial sums in FP64 (K*M terms), tree reduction.
+// Per (segment, plane) pair: energy = sum |Y|^2 and peak = max |Y|^2 over
+// the K*M envelope values (App. A optimal-plane selection).  Each pair is
+// split over kMetricChunks blocks so the read of Y runs at HBM speed; FP32
+// envelopes are squared in FP32 and summed in FP32 partials of at most 8
+// terms (relative error <= ~5e-7) before FP64 accumulation (the FP64 pipe is
+// slow on this part); FP64 envelopes stay in FP64.  Blocks combine with a
+// double atomicAdd and an integer atomicMax on the (non-negative) float bits;
+// both outputs are zeroed by the launcher first.
+constexpr int kMetricChunks = 64;
+
 template <typename V, int E>
 __global__ void __launch_bounds__(256) k_plane_metrics(const typename Env<V, E>::S* __restrict__ y, int64_t per_plane,
                                                        double* __restrict__ energy, float* __restrict__ peak) {
-  const int64_t pair = blockIdx.x;   // segment * P + plane
+  using R = decltype(V().x);
+  const int64_t pair = blockIdx.x / kMetricChunks;
+  const int part = (int)(blockIdx.x - pair * kMetricChunks);
+  const int64_t len = (per_plane + kMetricChunks - 1) / kMetricChunks;
+  const int64_t b0 = part * len, b1 = min(per_plane, b0 + len);
   const typename Env<V, E>::S* p = y + pair * per_plane;
   double e = 0.0;
   float mx = 0.0f;
-  for (int64_t i = threadIdx.x; i < per_plane; i += blockDim.x) {
-    const V v = Env<V, E>::from(stream_load(&p[i]));
-    const double a2 = (double)v.x * (double)v.x + (double)v.y * (double)v.y;
-    e += a2;
-    mx = fmaxf(mx, (float)a2);
-  }
-  __shared__ double se[256];
-  __shared__ float sm[256];
-  se[threadIdx.x] = e;
-  sm[threadIdx.x] = mx;
-  __syncthreads();
-  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-    if (threadIdx.x < s) {
-      se[threadIdx.x] += se[threadIdx.x + s];
-      sm[threadIdx.x] = fmaxf(sm[threadIdx.x], sm[threadIdx.x + s]);
+  for (int64_t i0 = b0 + threadIdx.x; i0 < b1; i0 += 8 * (int64_t)blockDim.x) {
+    R es = (R)0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int64_t i = i0 + (int64_t)u * blockDim.x;
+      if (i < b1) {
+        const V v = Env<V, E>::from(stream_load(&p[i]));
+        const R a2 = v.x * v.x + v.y * v.y;
+        es += a2;
+        mx = fmaxf(mx, (float)a2);
+      }
     }
-    __syncthreads();
+    e += (double)es;
   }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    e += __shfl_xor_sync(0xffffffffu, e, o);
+    mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  }
+  __shared__ double se[8];
+  __shared__ float sm[8];
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    se[w] = e;
+    sm[w] = mx;
+  }
+  __syncthreads();
   if (threadIdx.x == 0) {
-    energy[pair] = se[0];
-    peak[pair] = sm[0];
+    double et = 0.0;
+    float mt = 0.0f;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      et += se[k];
+      mt = fmaxf(mt, sm[k]);
+    }
+    atomicAdd(&energy[pair], et);
+    atomicMax(reinterpret_cast<int*>(&peak[pair]), __float_as_int(mt));
   }
 }
 
@@ -519,18 +605,22 @@ __global__ void __launch_bounds__(256) k_plane_metrics(const typename Env<V, E>:
 cudaError_t launch_plane_metrics(const void* y, int env, int64_t pairs, int64_t per_plane, double* energy, float* peak,
                                  cudaStream_t st) {
   if (pairs == 0) return cudaSuccess;
+  cudaError_t e0 = cudaMemsetAsync(energy, 0, (size_t)pairs * sizeof(double), st);
+  if (e0 == cudaSuccess) e0 = cudaMemsetAsync(peak, 0, (size_t)pairs * sizeof(float), st);
+  if (e0 != cudaSuccess) return e0;
+  const unsigned grid = (unsigned)(pairs * kMetricChunks);
   switch (env) {
     case ENV_F64:
-      k_plane_metrics<double2, ENV_F64><<<(unsigned)pairs, 256, 0, st>>>(static_cast<const double2*>(y), per_plane, energy, peak);
+      k_plane_metrics<double2, ENV_F64><<<grid, 256, 0, st>>>(static_cast<const double2*>(y), per_plane, energy, peak);
       break;
     case ENV_BF16:
-      k_plane_metrics<float2, ENV_BF16><<<(unsigned)pairs, 256, 0, st>>>(static_cast<const __nv_bfloat162*>(y), per_plane, energy, peak);
+      k_plane_metrics<float2, ENV_BF16><<<grid, 256, 0, st>>>(static_cast<const __nv_bfloat162*>(y), per_plane, energy, peak);
       break;
     case ENV_F16:
-      k_plane_metrics<float2, ENV_F16><<<(unsigned)pairs, 256, 0, st>>>(static_cast<const __half2*>(y), per_plane, energy, peak);
+      k_plane_metrics<float2, ENV_F16><<<grid, 256, 0, st>>>(static_cast<const __half2*>(y), per_plane, energy, peak);
       break;
     default:
-      k_plane_metrics<float2, ENV_F32><<<(unsigned)pairs, 256, 0, st>>>(static_cast<const float2*>(y), per_plane, energy, peak);
+      k_plane_metrics<float2, ENV_F32><<<grid, 256, 0, st>>>(static_cast<const float2*>(y), per_plane, energy, peak);
   }
   return cudaGetLastError();
 }
@@ -560,8 +650,11 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
   DenseArgs<T> da;
   da.remod = c.remod;
   if constexpr (sizeof(T) == 4) {
-    if (const RowVariant* v = c.remod ? nullptr : row_variant(c.variant))
-      return v->fwd[env](rows, n_rows, Nr, X, y, B, static_cast<const float2*>(c.stw), st);
+    if (const RowVariant* v = c.remod ? nullptr : row_variant(c.variant)) {
+      if (!wtab) return v->fwd[env](rows, n_rows, Nr, X, y, B, static_cast<const float2*>(c.stw), st);
+      if (env == ENV_F32 && v->fwd_tab)
+        return v->fwd_tab(rows, n_rows, Nr, X, y, B, static_cast<const float2*>(c.stw), st, wtab);
+    }
   }
   GenericEngine eng{c.rp};
   const unsigned blocks = (unsigned)units;
@@ -598,8 +691,11 @@ cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const in
   da.remod = c.remod;
   if (units == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (const RowVariant* v = (c.remod || da.divide) ? nullptr : row_variant(c.variant))
-      return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, static_cast<const float2*>(c.stw), st);
+    if (const RowVariant* v = (c.remod || da.divide) ? nullptr : row_variant(c.variant)) {
+      if (!wtab) return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, static_cast<const float2*>(c.stw), st);
+      if (env == ENV_F32 && v->inv_tab)
+        return v->inv_tab(rows, row_list, n_sel, n_rows, Nr, y, A, B, static_cast<const float2*>(c.stw), st, wtab);
+    }
   }
   GenericEngine eng{c.rp};
   const unsigned blocks = (unsigned)units;

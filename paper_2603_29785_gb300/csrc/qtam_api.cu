@@ -501,6 +501,15 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
   return QTAM_OK;
 }
 
+// A compile-time row variant serves a plan of its length with FP32 compute,
+// outside the dense mode; plans with a non-bisquare window need a variant
+// built for window tables and FP32 envelopes.
+bool variant_usable(const qtam_plan_s* pl, int id) {
+  const RowVariant* v = row_variant(id);
+  if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || pl->eps > 0 || pl->remod) return false;
+  return pl->all_bisquare() || (v->fwd_tab != nullptr && pl->env == QTAM_DTYPE_F32);
+}
+
 void free_plan(qtam_plan_s* pl) {
   if (!pl) return;
   if (pl->device >= 0) {
@@ -780,11 +789,10 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.variant = -1;
   pl->rc.tensor = pl->short_dft == QTAM_SHORT_DFT_TENSOR && tc_forward_supported(pl->M);
   pl->rc.remod = pl->remod;
-  const bool dense = pl->eps > 0 || pl->remod;   // runtime engine only
-  if (!dbl && pl->all_bisquare() && !dense) {   // compile-time variants hard-code the bisquare
+  if (!dbl) {
     for (int v = 0; v < row_variant_count(); ++v)
-      if (row_variant(v)->M == pl->M) {
-        pl->rc.variant = v;   // first registered variant for this length
+      if (variant_usable(pl, v)) {
+        pl->rc.variant = v;   // first registered usable variant for this length
         break;
       }
   }
@@ -867,9 +875,8 @@ qtam_status qtam_plan_variants(qtam_plan_t pl, int32_t* ids, int32_t capacity, i
     ++n;
   };
   push(-1);
-  if (pl->compute == QTAM_DTYPE_F32 && pl->all_bisquare() && !(pl->eps > 0 || pl->remod))
-    for (int v = 0; v < row_variant_count(); ++v)
-      if (row_variant(v)->M == pl->M) push(v);
+  for (int v = 0; v < row_variant_count(); ++v)
+    if (variant_usable(pl, v)) push(v);
   *count = n;
   return QTAM_OK;
 }
@@ -877,8 +884,7 @@ qtam_status qtam_plan_variants(qtam_plan_t pl, int32_t* ids, int32_t capacity, i
 qtam_status qtam_plan_set_variant(qtam_plan_t pl, int32_t id) {
   if (!pl) return fail(QTAM_ERR_INVALID_ARG, "plan is NULL");
   if (id != -1) {
-    const RowVariant* v = row_variant(id);
-    if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || !pl->all_bisquare() || pl->eps > 0 || pl->remod)
+    if (!variant_usable(pl, id))
       return fail(QTAM_ERR_INVALID_ARG, "variant does not match the plan's envelope length, dtype or window");
   }
   if (id >= 0 && pl->device >= 0) {

@@ -87,6 +87,11 @@ using RowFwdFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const float
                                  cudaStream_t);
 using RowInvFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
                                  const float2*, cudaStream_t);
+// the same with the plan's window table (non-bisquare windows), FP32 envelopes
+using RowFwdTabFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const float2*, void*, int64_t, const float2*,
+                                    cudaStream_t, const float*);
+using RowInvTabFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
+                                    const float2*, cudaStream_t, const float*);
 struct RowVariant {
   int M;
   int rows_per_block;
@@ -97,6 +102,8 @@ struct RowVariant {
   int r[kMaxStages];
   RowFwdFn fwd[4];
   RowInvFn inv[4];
+  RowFwdTabFn fwd_tab;   // null unless built for window tables (FP32 envelopes only)
+  RowInvTabFn inv_tab;
 };
 int row_variant_count();
 // per (segment, plane) pair: energy = sum |Y|^2 (FP64), peak = max |Y|^2 over K*M values

@@ -132,16 +132,20 @@ def test_window_argument_errors_and_variants():
     d = qtam.make_desc(*base)
     d.window = 7
     assert _err(lambda: qtam.qtam_plan(d, -1)) == 1
-    # compile-time row variants hard-code the bisquare: other windows run the runtime engine only
+    # compile-time row variants: the bisquare kernels evaluate the window formula; other windows use the
+    # variants built for window tables
     b = qtam.Plan(4096.0, 262144, (4, 8, 16, 32, 64), 20.0, 2048.0, 128, device=-1)
     h = qtam.Plan(4096.0, 262144, (4, 8, 16, 32, 64), 20.0, 2048.0, 128, window="hann", device=-1)
-    assert len(qtam.qtam_plan_variants(b.handle)) > 1 and b.info["row_variant"] >= 0
-    assert qtam.qtam_plan_variants(h.handle) == [-1] and h.info["row_variant"] == -1
-    assert _err(lambda: qtam.qtam_plan_set_variant(h.handle, qtam.qtam_plan_variants(b.handle)[1])) == 1
-    # a bank with one non-bisquare plane also runs the runtime engine only
+    vb, vh = qtam.qtam_plan_variants(b.handle), qtam.qtam_plan_variants(h.handle)
+    assert len(vb) > 2 and b.info["row_variant"] >= 0
+    # non-bisquare windows: the variants built for window tables (FP32 envelopes) only
+    assert vh[0] == -1 and 2 <= len(vh) < len(vb) and set(vh) <= set(vb) and h.info["row_variant"] == vh[1]
+    assert _err(lambda: qtam.qtam_plan_set_variant(h.handle, [v for v in vb if v not in vh][0])) == 1
+    hb = qtam.Plan(4096.0, 262144, (4, 8), 20.0, 2048.0, 128, window="hann", envelope="bf16", device=-1)
+    assert qtam.qtam_plan_variants(hb.handle) == [-1]                    # 16-bit envelopes: runtime engine
     m = qtam.Plan(4096.0, 262144, (4, 8), 20.0, 2048.0, 128, window=("bisquare", "tukey"), window_param=(0, 0.5),
                   device=-1)
-    assert qtam.qtam_plan_variants(m.handle) == [-1]
+    assert qtam.qtam_plan_variants(m.handle) == vh
     assert _err(lambda: qtam.Plan(*base[:2], (8, 16), *base[3:], window=("hann", "tukey"),
                                   window_param=(0.0, 2.0), device=-1)) == 1
     with pytest.raises(ValueError):

@@ -381,7 +381,8 @@ def test_plane_metrics_and_optimal_plane():
         assert np.allclose(energy[b].cpu().numpy(), e, rtol=2e-6)
         assert np.allclose(peak[b].cpu().numpy(), pk, rtol=5e-6)
         e_gpu, pk_gpu, _, _ = O.plane_metrics(Yg[b])          # same reduction of the GPU envelopes
-        assert np.allclose(energy[b].cpu().numpy(), e_gpu, rtol=1e-9)
+        # FP32 squares summed in short FP32 partials, then FP64 (relative error <= ~5e-7)
+        assert np.allclose(energy[b].cpu().numpy(), e_gpu, rtol=1e-6)
         assert int(best_e[b]) == int(np.argmax(e_gpu)) and int(best_p[b]) == int(np.argmax(pk_gpu))
 
 
