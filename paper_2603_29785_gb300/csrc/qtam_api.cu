@@ -207,6 +207,11 @@ struct qtam_plan_s {
   void* d_stw_row = nullptr;
   std::mutex mu;
   std::map<uint64_t, MaskEntry> masks;
+  // host round trip pipeline: copy-in and copy-out streams and their events,
+  // created on first use; one round trip at a time per plan (rt_mu)
+  std::mutex rt_mu;
+  cudaStream_t rt_in = nullptr, rt_out = nullptr;
+  std::vector<cudaEvent_t> rt_ev;
 
   size_t real_size() const { return compute == QTAM_DTYPE_F64 ? 8 : 4; }
   size_t cplx_size() const { return 2 * real_size(); }
@@ -526,6 +531,9 @@ void free_plan(qtam_plan_s* pl) {
     cudaFree(pl->d_stw_col);
     cudaFree(pl->d_stw_row);
     for (auto& kv : pl->variant_tw) cudaFree(kv.second);
+    for (cudaEvent_t e : pl->rt_ev) cudaEventDestroy(e);
+    if (pl->rt_in) cudaStreamDestroy(pl->rt_in);
+    if (pl->rt_out) cudaStreamDestroy(pl->rt_out);
     for (auto& kv : pl->masks) {
       cudaFree(kv.second.invP);
       cudaFree(kv.second.rows);
@@ -1079,16 +1087,59 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
                                 void* x_dev, void* y_dev, void* xhat_dev, void* ws, size_t wsb, void* stream) {
   qtam_status s = common_checks(pl, B);
   if (s != QTAM_OK || B == 0) return s;
-  if (!x_host || !xhat_host) return fail(QTAM_ERR_INVALID_ARG, "NULL host buffer");
+  if (!x_host || !xhat_host || !x_dev || !y_dev || !xhat_dev) return fail(QTAM_ERR_INVALID_ARG, "NULL buffer");
+  if (wsb < ws_bytes(pl, B)) return fail(QTAM_ERR_WORKSPACE, "workspace too small");
   DeviceGuard g(pl->device);
+  std::lock_guard<std::mutex> lk(pl->rt_mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const size_t xb = (size_t)B * pl->N * pl->real_size();
-  cudaError_t e = cudaMemcpyAsync(x_dev, x_host, xb, cudaMemcpyHostToDevice, st);
-  if (e != cudaSuccess) return fail_cuda(e, "host-to-device copy");
-  if ((s = qtam_forward(pl, x_dev, B, y_dev, ws, wsb, stream)) != QTAM_OK) return s;
-  if ((s = qtam_inverse(pl, y_dev, B, mask, xhat_dev, ws, wsb, stream)) != QTAM_OK) return s;
-  e = cudaMemcpyAsync(xhat_host, xhat_dev, xb, cudaMemcpyDeviceToHost, st);
-  if (e != cudaSuccess) return fail_cuda(e, "device-to-host copy");
+  constexpr int kChunks = 8;
+  cudaError_t e = cudaSuccess;
+  if (!pl->rt_in) {
+    e = cudaStreamCreateWithFlags(&pl->rt_in, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->rt_out, cudaStreamNonBlocking);
+    for (int i = 0; i < 2 * kChunks + 2 && e == cudaSuccess; ++i) {
+      cudaEvent_t ev;
+      e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+      if (e == cudaSuccess) pl->rt_ev.push_back(ev);
+    }
+    if (e != cudaSuccess) return fail_cuda(e, "round-trip streams");
+  }
+  // chunk c of C holds segments [s0, s0 + nb); copies of neighbouring chunks
+  // overlap the transforms of chunk c on the caller's stream
+  const int C = (int)std::min<int64_t>(B, kChunks);
+  const size_t xs = (size_t)pl->N * pl->real_size();
+  const size_t ys = (size_t)pl->P * pl->K * pl->M * pl->env_size();
+  cudaEvent_t ev_start = pl->rt_ev[0], ev_end = pl->rt_ev[1];
+  cudaEvent_t* ev_in = &pl->rt_ev[2];
+  cudaEvent_t* ev_done = &pl->rt_ev[2 + kChunks];
+  auto seg0 = [&](int c) { return (int64_t)c * (B / C) + std::min<int64_t>(c, B % C); };
+  if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess) return fail_cuda(e, "cudaEventRecord");
+  if ((e = cudaStreamWaitEvent(pl->rt_in, ev_start, 0)) != cudaSuccess ||
+      (e = cudaStreamWaitEvent(pl->rt_out, ev_start, 0)) != cudaSuccess)
+    return fail_cuda(e, "cudaStreamWaitEvent");
+  for (int c = 0; c < C; ++c) {
+    const int64_t s0 = seg0(c), nb = seg0(c + 1) - s0;
+    e = cudaMemcpyAsync(static_cast<char*>(x_dev) + s0 * xs, static_cast<const char*>(x_host) + s0 * xs, nb * xs,
+                        cudaMemcpyHostToDevice, pl->rt_in);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_in[c], pl->rt_in);
+    if (e != cudaSuccess) return fail_cuda(e, "host-to-device copy");
+  }
+  for (int c = 0; c < C; ++c) {
+    const int64_t s0 = seg0(c), nb = seg0(c + 1) - s0;
+    if ((e = cudaStreamWaitEvent(st, ev_in[c], 0)) != cudaSuccess) return fail_cuda(e, "cudaStreamWaitEvent");
+    void* xc = static_cast<char*>(x_dev) + s0 * xs;
+    void* yc = static_cast<char*>(y_dev) + s0 * ys;
+    void* hc = static_cast<char*>(xhat_dev) + s0 * xs;
+    if ((s = qtam_forward(pl, xc, nb, yc, ws, wsb, stream)) != QTAM_OK) return s;
+    if ((s = qtam_inverse(pl, yc, nb, mask, hc, ws, wsb, stream)) != QTAM_OK) return s;
+    if ((e = cudaEventRecord(ev_done[c], st)) != cudaSuccess ||
+        (e = cudaStreamWaitEvent(pl->rt_out, ev_done[c], 0)) != cudaSuccess)
+      return fail_cuda(e, "chunk ordering");
+    e = cudaMemcpyAsync(static_cast<char*>(xhat_host) + s0 * xs, hc, nb * xs, cudaMemcpyDeviceToHost, pl->rt_out);
+    if (e != cudaSuccess) return fail_cuda(e, "device-to-host copy");
+  }
+  if ((e = cudaEventRecord(ev_end, pl->rt_out)) != cudaSuccess || (e = cudaStreamWaitEvent(st, ev_end, 0)) != cudaSuccess)
+    return fail_cuda(e, "round-trip join");
   e = cudaStreamSynchronize(st);
   if (e != cudaSuccess) return fail_cuda(e, "cudaStreamSynchronize");
   return QTAM_OK;
