@@ -230,13 +230,14 @@ QTAM_API qtam_status qtam_inverse_single_tile(qtam_plan_t plan, const void* y, i
 /* Forward then inverse from HOST buffers: copies x_host into x_dev, runs
  * qtam_forward into y_dev and qtam_inverse into xhat_dev, and copies xhat_dev
  * back into xhat_host; synchronises `stream` before returning.  The batch is
- * split into up to 8 chunks: host-to-device copies run on one library-owned
- * stream and device-to-host copies on another, ordered against the
- * transforms on `stream` by events, so the copies of neighbouring chunks
- * overlap the transforms (pinned host buffers make the copies asynchronous).
- * One round trip at a time per plan (calls on the same plan serialise).
- * All device buffers are caller-owned ([batch][N], [batch][P][K][M],
- * [batch][N]); workspace as for qtam_forward with `batch` segments. */
+ * split into chunks of about 16 MB of input (at most 8): host-to-device
+ * copies run on one library-owned stream and device-to-host copies on
+ * another, ordered against the transforms on `stream` by events, so the
+ * copies of neighbouring chunks overlap the transforms (pinned host buffers
+ * make the copies asynchronous).  One round trip at a time per plan (calls
+ * on the same plan serialise).  All device buffers are caller-owned
+ * ([batch][N], [batch][P][K][M], [batch][N]); workspace as for qtam_forward
+ * with `batch` segments. */
 QTAM_API qtam_status qtam_roundtrip_host(qtam_plan_t plan, const void* x_host, int64_t batch, uint64_t plane_mask,
                                 void* xhat_host, void* x_dev, void* y_dev, void* xhat_dev,
                                 void* workspace, size_t workspace_bytes, void* stream);

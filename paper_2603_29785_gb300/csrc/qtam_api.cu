@@ -1105,9 +1105,12 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
     if (e != cudaSuccess) return fail_cuda(e, "round-trip streams");
   }
   // chunk c of C holds segments [s0, s0 + nb); copies of neighbouring chunks
-  // overlap the transforms of chunk c on the caller's stream
-  const int C = (int)std::min<int64_t>(B, kChunks);
+  // overlap the transforms of chunk c on the caller's stream.  Chunks of about
+  // 16 MB of input: smaller ones expose less copy time at the ends but pay
+  // per-chunk launch and tail costs (measured best on the 64 s workload)
   const size_t xs = (size_t)pl->N * pl->real_size();
+  const int64_t by_bytes = (int64_t)((size_t)B * xs / (16u << 20));
+  const int C = (int)std::max<int64_t>(1, std::min<int64_t>({B, (int64_t)kChunks, by_bytes}));
   const size_t ys = (size_t)pl->P * pl->K * pl->M * pl->env_size();
   cudaEvent_t ev_start = pl->rt_ev[0], ev_end = pl->rt_ev[1];
   cudaEvent_t* ev_in = &pl->rt_ev[2];

@@ -358,6 +358,29 @@ def test_roundtrip_host_entry(B):
     assert torch.equal(y_dev, p.forward(torch.from_numpy(x).cuda()))
 
 
+def test_roundtrip_host_pipelined_chunks(cfg2):
+    """50 segments of 64 s (1 MiB each): three uneven chunks of the host round
+    trip; every segment equals the device path and sampled ones the oracle."""
+    p, g, _ = cfg2
+    B = 50
+    x = np.stack([synth.white(900 + b, g.N) for b in range(B)]).astype(np.float32)
+    x_pinned = torch.from_numpy(x).pin_memory()
+    xh_pinned = torch.empty((B, g.N), dtype=torch.float32).pin_memory()
+    x_dev = torch.empty((B, g.N), dtype=torch.float32, device="cuda")
+    xh_dev = torch.empty_like(x_dev)
+    y_dev = p.envelope_tensor(B)
+    ws, wsb = p.workspace(B)
+    qtam.qtam_roundtrip_host(p.handle, x_pinned, B, 0, xh_pinned, x_dev, y_dev, xh_dev, ws, wsb)
+    xd = torch.from_numpy(x).cuda()
+    yd = p.forward(xd)
+    assert torch.equal(y_dev, yd)
+    ref = host(p.inverse(yd)).astype(np.float64)
+    xh = xh_pinned.numpy().astype(np.float64)
+    assert max(rel(xh[b], ref[b]) for b in range(B)) < 1e-6     # the inverse accumulates with float atomics
+    for b in (0, 17, 49):
+        assert rel(xh[b], O.projection(g, x[b].astype(np.float64), tau=p.info["p_floor_rel"])) < RT["f32"]
+
+
 def test_device_errors_are_reported():
     p = make(**SMALL[0])
     with pytest.raises(qtam.QtamError) as e:
