@@ -171,7 +171,7 @@ def measured_traffic(kernel: str):
     try:
         tr = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))
         h = hashlib.sha256()
-        for f in ("kernels_rows.cu", "fft_static.cuh", "fft_core.cuh", "qtam_internal.h"):
+        for f in ("kernels_rows.cu", "rows_common.cuh", "fft_static.cuh", "fft_core.cuh", "qtam_internal.h"):
             h.update(open(os.path.join(ROOT, "paper_2603_29785_gb300", "csrc", f), "rb").read())
         if h.hexdigest() != tr.get("source_sha256"):
             return None
