@@ -635,6 +635,58 @@ qtam_status get_mask(qtam_plan_s* pl, uint64_t mask, MaskEntry** me) {
 }  // namespace
 
 namespace qtam {
+namespace {
+const StreamRowFns* fused_fns(const qtam_plan_s* pl) {
+  if (pl->compute != QTAM_DTYPE_F32 || pl->env != QTAM_DTYPE_F32 || !pl->all_bisquare() || pl->rc.tensor ||
+      pl->eps > 0 || pl->remod || pl->device < 0)
+    return nullptr;
+  const RowVariant* v = row_variant(pl->rc.variant);
+  return v && pl->rc.stw ? stream_row_fns(v->name) : nullptr;
+}
+}  // namespace
+
+qtam_status stream_forward_fused(qtam_plan_s* pl, const void* x, int64_t b, void* ymap, int64_t pitch, int Gm, int Hn,
+                                 const void* phase, void* ws, size_t wsb, cudaStream_t st, bool* used) {
+  *used = false;
+  const StreamRowFns* f = fused_fns(pl);
+  if (!f || b == 0) return QTAM_OK;
+  if (wsb < ws_bytes(pl, b)) return fail(QTAM_ERR_WORKSPACE, "workspace too small");
+  DeviceGuard g(pl->device);
+  Regions rg = split_ws(pl, ws, b);
+  qtam_status s = run_spectrum<float>(pl, x, b, rg.r0, ws, st);
+  if (s != QTAM_OK) return s;
+  cudaError_t e = f->fwd(static_cast<const RowDev<float>*>(pl->d_rows), pl->P * pl->K, pl->Nr,
+                         static_cast<const float2*>(rg.r0), static_cast<float2*>(ymap), pitch, Gm, Hn,
+                         static_cast<const float2*>(phase), b, static_cast<const float2*>(pl->rc.stw), st);
+  if (e != cudaSuccess) return fail_cuda(e, "fused stream forward");
+  *used = true;
+  return QTAM_OK;
+}
+
+qtam_status stream_inverse_fused(qtam_plan_s* pl, const void* hist, int hcols, const void* ynew, int64_t pitch, int Hn,
+                                 const void* phase, int64_t b, uint64_t mask, void* x, void* ws, size_t wsb,
+                                 cudaStream_t st, bool* used) {
+  *used = false;
+  const StreamRowFns* f = fused_fns(pl);
+  if (!f || b == 0) return QTAM_OK;
+  if (wsb < ws_bytes(pl, b)) return fail(QTAM_ERR_WORKSPACE, "workspace too small");
+  MaskEntry* me = nullptr;
+  qtam_status s = get_mask(pl, mask, &me);
+  if (s != QTAM_OK) return s;
+  DeviceGuard g(pl->device);
+  Regions rg = split_ws(pl, ws, b);
+  cudaError_t e = cudaMemsetAsync(rg.r0, 0, (size_t)b * pl->Nr * sizeof(float2), st);
+  if (e == cudaSuccess)
+    e = f->inv(static_cast<const RowDev<float>*>(pl->d_rows), me->rows, me->n_sel, pl->P * pl->K, pl->Nr,
+               static_cast<const float2*>(hist), hcols, static_cast<const float2*>(ynew), pitch, Hn,
+               static_cast<const float2*>(phase), static_cast<float2*>(rg.r0), b,
+               static_cast<const float2*>(pl->rc.stw), st);
+  if (e != cudaSuccess) return fail_cuda(e, "fused stream inverse");
+  if ((s = run_synthesize<float>(pl, rg.r0, b, me, x, ws, st)) != QTAM_OK) return s;
+  *used = true;
+  return QTAM_OK;
+}
+
 void set_last_error(const std::string& msg) { g_last_error = msg; }
 int plan_device(const qtam_plan_s* plan) { return plan ? plan->device : -1; }
 }  // namespace qtam

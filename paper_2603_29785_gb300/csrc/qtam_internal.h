@@ -8,6 +8,7 @@
 #include <string>
 
 #include "fft_core.cuh"
+#include "../../include/qtam.h"
 
 struct qtam_plan_s;
 
@@ -105,6 +106,32 @@ struct RowVariant {
   RowFwdTabFn fwd_tab;   // null unless built for window tables (FP32 envelopes only)
   RowInvTabFn inv_tab;
 };
+// Fused streaming row kernels (kernels_rows_stream.cu) of a compile-time
+// variant, looked up by the variant's name: forward with the crop-and-phase
+// store into the map, inverse with the history/new-columns chunk load.
+using StreamFwdFn = cudaError_t (*)(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, float2* y,
+                                    int64_t pitch, int Gm, int Hn, const float2* phase, int64_t B, const float2* twM,
+                                    cudaStream_t st);
+using StreamInvFn = cudaError_t (*)(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
+                                    const float2* hist, int hcols, const float2* ynew, int64_t pitch, int Hn,
+                                    const float2* phase, float2* A, int64_t B, const float2* twM, cudaStream_t st);
+struct StreamRowFns {
+  const char* name;
+  StreamFwdFn fwd;
+  StreamInvFn inv;
+};
+const StreamRowFns* stream_row_fns(const char* variant_name);
+
+// Streaming steps with the fused row kernels (qtam_api.cu, used by
+// qtam_stream.cu).  *used is false (and nothing is launched) when the plan
+// has no fused kernels: F32 compute and envelopes, bisquare windows, a
+// compile-time variant with a fused entry.  phase is [b][P K] complex FP32.
+qtam_status stream_forward_fused(qtam_plan_s* pl, const void* x, int64_t b, void* ymap, int64_t pitch, int Gm, int Hn,
+                                 const void* phase, void* ws, size_t wsb, cudaStream_t st, bool* used);
+qtam_status stream_inverse_fused(qtam_plan_s* pl, const void* hist, int hcols, const void* ynew, int64_t pitch, int Hn,
+                                 const void* phase, int64_t b, uint64_t mask, void* x, void* ws, size_t wsb,
+                                 cudaStream_t st, bool* used);
+
 int row_variant_count();
 // per (segment, plane) pair: energy = sum |Y|^2 (FP64), peak = max |Y|^2 over K*M values
 cudaError_t launch_plane_metrics(const void* y, int env, int64_t pairs, int64_t per_plane, double* energy, float* peak,

@@ -122,6 +122,22 @@ __global__ void k_stream_gather_y(const S* __restrict__ hist, int hcols, const S
   }
 }
 
+// phase[i][r] = exp(sign 2 pi i kc[r] (a0 + i hop) / N): the per-(chunk, row)
+// factors of the fused streaming kernels, one FP64 evaluation each
+__global__ void k_stream_phases(const int* __restrict__ kc, int R, int64_t b, int64_t N, int64_t a0, int64_t hop,
+                                double sign, float2* __restrict__ phase) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= b * R) return;
+  const int64_t i = e / R;
+  const int r = (int)(e - i * R);
+  int64_t am = (a0 + i * hop) % N;
+  if (am < 0) am += N;
+  const int64_t m = ((int64_t)kc[r] * am) % N;
+  double s, c;
+  sincospi(sign * 2.0 * (double)m / (double)N, &s, &c);
+  phase[e] = make_float2((float)c, (float)s);
+}
+
 template <typename S>
 cudaError_t crop(const void* env, int64_t b, int R, int M, int Gm, int Hn, const int* kc, int64_t N, int64_t a0,
                  int64_t hop, void* y, int64_t pitch, cudaStream_t st) {
@@ -180,6 +196,7 @@ struct qtam_stream_s {
   void* ws = nullptr;
   size_t wsb = 0;
   int* kc = nullptr;
+  float2* phase = nullptr;   // [max_chunks][R] phases of the fused kernels
   size_t bytes = 0;
 };
 
@@ -189,7 +206,8 @@ void free_stream(qtam_stream_s* s) {
   if (!s) return;
   if (s->device >= 0) {
     DevScope g(s->device);
-    for (void* p : {s->hx[0], s->hx[1], s->hy[0], s->hy[1], s->chunks, s->envb, s->ws, (void*)s->kc}) cudaFree(p);
+    for (void* p : {s->hx[0], s->hx[1], s->hy[0], s->hy[1], s->chunks, s->envb, s->ws, (void*)s->kc, (void*)s->phase})
+      cudaFree(p);
   }
   delete s;
 }
@@ -225,6 +243,12 @@ cudaError_t launch_gather_y(const qtam_stream_s* s, const void* ynew, int64_t pi
       return gather_y<__half2>(h, hc, ynew, pitch, b, s->R, s->M, s->Hn, s->kc, s->N, a0, s->hop, s->envb, st);
     default: return gather_y<float2>(h, hc, ynew, pitch, b, s->R, s->M, s->Hn, s->kc, s->N, a0, s->hop, s->envb, st);
   }
+}
+
+cudaError_t launch_phases(const qtam_stream_s* s, int64_t b, int64_t a0, double sign, cudaStream_t st) {
+  const int64_t n = b * s->R;
+  k_stream_phases<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(s->kc, s->R, b, s->N, a0, s->hop, sign, s->phase);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_gather_x(const qtam_stream_s* s, const void* xnew, int64_t b, cudaStream_t st) {
@@ -302,7 +326,8 @@ qtam_status qtam_stream_create(qtam_plan_t plan, int64_t hop, int64_t max_chunks
       (st = salloc(s, &s->chunks, (size_t)max_chunks * N * s->rs)) != QTAM_OK ||
       (st = salloc(s, &s->envb, (size_t)max_chunks * R * M * s->es)) != QTAM_OK ||
       (st = salloc(s, &s->ws, wsb)) != QTAM_OK ||
-      (st = salloc(s, reinterpret_cast<void**>(&s->kc), (size_t)R * sizeof(int))) != QTAM_OK) {
+      (st = salloc(s, reinterpret_cast<void**>(&s->kc), (size_t)R * sizeof(int))) != QTAM_OK ||
+      (st = salloc(s, reinterpret_cast<void**>(&s->phase), (size_t)max_chunks * R * sizeof(float2))) != QTAM_OK) {
     free_stream(s);
     return st;
   }
@@ -347,10 +372,20 @@ qtam_status qtam_stream_forward(qtam_stream_t s, const void* x, int64_t n, void*
     const char* xb = static_cast<const char*>(x) + (size_t)(done * s->hop) * s->rs;
     cudaError_t e = launch_gather_x(s, xb, b, st);
     if (e != cudaSuccess) return sfail_cuda(e, "stream gather");
-    qtam_status q = qtam_forward(s->plan, s->chunks, b, s->envb, s->ws, s->wsb, stream);
-    if (q != QTAM_OK) return q;
-    e = launch_crop(s, b, s->pos - nh, static_cast<char*>(y) + (size_t)(done * s->Hn) * s->es, pitch, st);
-    if (e != cudaSuccess) return sfail_cuda(e, "stream crop");
+    void* yout = static_cast<char*>(y) + (size_t)(done * s->Hn) * s->es;
+    bool used = false;
+    if (s->env == QTAM_DTYPE_F32) {   // fused: the row kernel stores the kept columns with the phase
+      if ((e = launch_phases(s, b, s->pos - nh, -1.0, st)) != cudaSuccess) return sfail_cuda(e, "stream phases");
+      qtam_status q = qtam::stream_forward_fused(s->plan, s->chunks, b, yout, pitch, s->Gm, s->Hn, s->phase, s->ws,
+                                                 s->wsb, st, &used);
+      if (q != QTAM_OK) return q;
+    }
+    if (!used) {
+      qtam_status q = qtam_forward(s->plan, s->chunks, b, s->envb, s->ws, s->wsb, stream);
+      if (q != QTAM_OK) return q;
+      e = launch_crop(s, b, s->pos - nh, yout, pitch, st);
+      if (e != cudaSuccess) return sfail_cuda(e, "stream crop");
+    }
     if (nh > 0) {  // history <- last 2G samples of [history | this step's samples]
       const int64_t nn = b * s->hop;
       char* dst = static_cast<char*>(s->hx[1 - s->cx]);
@@ -385,10 +420,20 @@ qtam_status qtam_stream_inverse(qtam_stream_t s, const void* y, int64_t n_cols, 
     const int64_t b = std::min(s->bmax, J - done);
     const char* yb = static_cast<const char*>(y) + (size_t)(done * s->Hn) * s->es;
     const int64_t a0 = (s->cpos / s->Hn) * s->hop - 3 * s->G;
-    cudaError_t e = launch_gather_y(s, yb, n_cols, b, a0, st);
-    if (e != cudaSuccess) return sfail_cuda(e, "stream re-chunk");
-    qtam_status q = qtam_inverse(s->plan, s->envb, b, plane_mask, s->chunks, s->ws, s->wsb, stream);
-    if (q != QTAM_OK) return q;
+    cudaError_t e = cudaSuccess;
+    bool used = false;
+    if (s->env == QTAM_DTYPE_F32) {   // fused: the row kernel reads history and new columns with the phase
+      if ((e = launch_phases(s, b, a0, 1.0, st)) != cudaSuccess) return sfail_cuda(e, "stream phases");
+      qtam_status q = qtam::stream_inverse_fused(s->plan, s->hy[s->cy], 2 * s->Gm, yb, n_cols, s->Hn, s->phase, b,
+                                                 plane_mask, s->chunks, s->ws, s->wsb, st, &used);
+      if (q != QTAM_OK) return q;
+    }
+    if (!used) {
+      e = launch_gather_y(s, yb, n_cols, b, a0, st);
+      if (e != cudaSuccess) return sfail_cuda(e, "stream re-chunk");
+      qtam_status q = qtam_inverse(s->plan, s->envb, b, plane_mask, s->chunks, s->ws, s->wsb, stream);
+      if (q != QTAM_OK) return q;
+    }
     e = cudaMemcpy2DAsync(static_cast<char*>(x) + (size_t)(done * s->hop) * s->rs, (size_t)s->hop * s->rs,
                           static_cast<const char*>(s->chunks) + (size_t)s->G * s->rs, (size_t)s->N * s->rs,
                           (size_t)s->hop * s->rs, (size_t)b, cudaMemcpyDeviceToDevice, st);

@@ -139,3 +139,30 @@ def test_stream_full_size_chunks():
     xh = _np(s.inverse(Y))
     xo = O.stream_inverse(g, Yg, 131072, tau=p.info["p_floor_rel"])
     assert _rel(xh, xo) < 1e-5
+
+
+def test_stream_fused_row_kernels_m600():
+    """N = 32768 chunks at 4096 Hz, Q {8,16,32} x 128 rows (M = 600, quantum 4096
+    samples): the compile-time variant's fused streaming kernels (crop-and-phase
+    store, history/new-columns load) against the oracle, push-size invariance
+    and a plane-masked inverse."""
+    cfg = dict(fs=4096.0, N=32768, qs=(8.0, 16.0, 32.0), fmin=20.0, fmax=2048.0, K=128)
+    p, g = _plan(cfg)
+    assert p.M == 600 and p.info["row_variant"] >= 0
+    hop = 16384
+    J = 12
+    x = np.concatenate([synth.glitchy_segment(40 + i, hop, 4096.0, chirp=(i % 3 == 0)) for i in range(J)])
+    xd = torch.from_numpy(x.astype(np.float32)).cuda()
+    s1 = qtam.Stream(p, hop=hop, max_chunks=5)
+    s2 = qtam.Stream(p, hop=hop, max_chunks=12)
+    Y = _push(s1, xd, [2, 5, 1, 4])
+    assert torch.equal(Y, s2.forward(xd))
+    Yg = _np(Y)
+    Yo = O.stream_forward(g, x.astype(np.float64), hop)
+    assert _rel(Yg, Yo) < 1e-6
+    assert np.max(np.abs(Yg - Yo)) <= 1e-5 * np.max(np.abs(Yo))
+    xh = _np(_push_inv(s1, Y, [3, 3, 6]))
+    tau = p.info["p_floor_rel"]
+    assert _rel(xh, O.stream_inverse(g, Yg, hop, tau=tau)) < 1e-5
+    xm = _np(s2.inverse(Y, plane_mask=0b010))
+    assert _rel(xm, O.stream_inverse(g, Yg, hop, planes=[1], tau=tau)) < 1e-5
