@@ -363,7 +363,10 @@ QTAM_API qtam_status qtam_stream_destroy(qtam_stream_t s);
  * building block of the tensor-core short DFT: D[128][N] = A[128][K] *
  * B[N][K]^T with A, B row-major BF16 (raw 16-bit patterns) and D row-major
  * FP32, all device buffers owned by the caller; flags bit 0 negates A, bit 1
- * negates B, bit 2 stages A in the M-major shared-memory layout.  N, K multiples of 16 in [16, 256]; A, B 16-byte aligned.
+ * negates B, bit 2 stages A in the M-major shared-memory layout, bit 3
+ * issues no MMA so the bounded completion wait runs out after about 1 ms
+ * (the timeout path: counted by qtam_tc_status, tensor memory released, D
+ * left untouched, the context stays usable).  N, K multiples of 16 in [16, 256]; A, B 16-byte aligned.
  * Enqueued on `stream`; a tensor-core wait that runs out (about 1 s) is
  * counted and reported by qtam_tc_status. */
 QTAM_API qtam_status qtam_tc_gemm_check(const void* A, const void* B, float* D, int32_t N, int32_t K, int32_t flags,

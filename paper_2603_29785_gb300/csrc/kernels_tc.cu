@@ -19,9 +19,11 @@ __device__ int g_tc_timeouts = 0;   // bounded tensor-core waits that ran out (r
 // One CTA of 128 threads: D[128][N] = (+/-A)[128][K] (+/-B)[N][K]^T with A, B
 // row-major BF16 in global memory, packed into the core-matrix layout in
 // shared memory, one MMA per K = 16, the accumulator in tensor memory.
+// flags bit 3 issues no MMA and no commit, so the completion wait runs out
+// after wait_cycles: the timeout path (counter, TMEM freed, clean return).
 __global__ void __launch_bounds__(128, 1)
     k_tc_gemm_check(const uint16_t* __restrict__ A, const uint16_t* __restrict__ B, float* __restrict__ D, int N,
-                    int K, uint32_t flags) {
+                    int K, uint32_t flags, long long wait_cycles) {
   extern __shared__ __align__(1024) unsigned char sm[];
   __shared__ __align__(8) uint64_t mbar;
   __shared__ uint32_t tslot;
@@ -59,7 +61,8 @@ __global__ void __launch_bounds__(128, 1)
   __syncthreads();
   tc::fence_after_sync();
   const uint32_t tbase = tslot;
-  if (threadIdx.x == 0) {
+  const bool issue = !(flags & 8u);
+  if (threadIdx.x == 0 && issue) {
     const uint32_t idesc = tc::make_idesc_bf16(128, N, flags & 1u, flags & 2u, flags & 4u);
     const uint32_t a0 = tc::smem_addr(sA), b0 = tc::smem_addr(sB), sbo = (uint32_t)K8 * 128u;
     for (int s = 0; s < K / 16; ++s)
@@ -67,7 +70,7 @@ __global__ void __launch_bounds__(128, 1)
                    s > 0);
     tc::mma_commit(&mbar);
   }
-  bool ok = tc::mbar_wait_bounded(&mbar, 0, tc::kWaitCycles);
+  bool ok = tc::mbar_wait_bounded(&mbar, 0, wait_cycles);
   tc::fence_after_sync();
   if (ok) {
     const int row = threadIdx.x;   // warp w reads lanes 32w .. 32w+31
@@ -79,7 +82,7 @@ __global__ void __launch_bounds__(128, 1)
     }
   } else {
     if (threadIdx.x == 0) atomicAdd(&g_tc_timeouts, 1);
-    tc::mbar_wait_bounded(&mbar, 0, tc::kWaitCycles);   // give an MMA still in flight a last chance
+    if (issue) tc::mbar_wait_bounded(&mbar, 0, wait_cycles);   // give an MMA still in flight a last chance
   }
   tc::fence_before_sync();
   __syncthreads();
@@ -407,8 +410,8 @@ qtam_status qtam_tc_gemm_check(const void* A, const void* B, float* D, int32_t N
     qtam::set_last_error("NULL buffer");
     return QTAM_ERR_INVALID_ARG;
   }
-  if (N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16 || (flags & ~7)) {
-    qtam::set_last_error("N and K must be multiples of 16 in [16, 256]; flags in {0..7}");
+  if (N < 16 || N > 256 || N % 16 || K < 16 || K > 256 || K % 16 || (flags & ~15)) {
+    qtam::set_last_error("N and K must be multiples of 16 in [16, 256]; flags in {0..15}");
     return QTAM_ERR_INVALID_ARG;
   }
   if ((reinterpret_cast<uintptr_t>(A) | reinterpret_cast<uintptr_t>(B)) & 15) {
@@ -420,8 +423,9 @@ qtam_status qtam_tc_gemm_check(const void* A, const void* B, float* D, int32_t N
   const size_t smem = (size_t)(128 + N) * K * 2 + 32768;
   cudaError_t e = qtam::allow_smem((const void*)qtam::k_tc_gemm_check, smem);
   if (e == cudaSuccess) {
+    const long long wait_cycles = (flags & 8) ? 2000000LL : qtam::tc::kWaitCycles;   // ~1 ms for the timeout test
     qtam::k_tc_gemm_check<<<1, 128, smem, static_cast<cudaStream_t>(stream)>>>(
-        static_cast<const uint16_t*>(A), static_cast<const uint16_t*>(B), D, N, K, (uint32_t)flags);
+        static_cast<const uint16_t*>(A), static_cast<const uint16_t*>(B), D, N, K, (uint32_t)flags, wait_cycles);
     e = cudaGetLastError();
   }
   if (e != cudaSuccess) {
