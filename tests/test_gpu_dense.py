@@ -85,3 +85,17 @@ def test_single_tile_needs_dense_mode():
     q = qtam.Plan(4096.0, 8192, (8.0,), 20.0, 2048.0, 32, stopband_eps=1e-3, device=0)
     with pytest.raises(qtam.QtamError):
         q.inverse_single_tile(q.envelope_tensor(1), 0, 32)          # row out of range
+
+
+def test_all_ones_window_tile_is_the_analytic_signal_gpu():
+    """The oracle pin's special case on the GPU (runtime engine, dense mode)."""
+    N = 512
+    p = qtam.Plan(64.0, N, (1.0,), 7.0, 7.0, 1, norm="none", window="tukey", window_param=0.0, stopband_eps=1.0,
+                  remodulate=True, n_out=N, device=0)
+    x = (synth.white(72, N) + 0.3).astype(np.float32)
+    T = p.forward(torch.from_numpy(x[None]).cuda()).cpu().numpy()[0, 0, 0].astype(np.complex128)
+    xd = x.astype(np.float64)
+    X = np.fft.rfft(xd)
+    n = np.arange(N)
+    expect = 0.5 * (xd + (X[0].real + X[-1].real * (-1.0) ** n) / N)
+    assert np.max(np.abs(T.real - expect)) <= 1e-6 * np.max(np.abs(xd))

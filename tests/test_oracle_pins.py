@@ -559,3 +559,20 @@ def test_small_stopband_barely_changes_the_tile():
     Y0, Y1 = O.forward(g0, x), O.forward(g1, x)
     assert np.linalg.norm(Y1 - Y0) <= 1e-9 * np.max(g1.c) * np.linalg.norm(np.fft.rfft(x)) * np.sqrt(g1.P * g1.K)
     assert np.linalg.norm(Y1 - Y0) > 0
+
+
+def test_all_ones_window_tile_is_the_analytic_signal():
+    """Textbook special case: one row whose window is 1 on every bin (a
+    rectangle, Tukey a = 0, with floor eps = 1 outside), c = 1, the carrier
+    restored, M = N.  The tile is (1/N) sum_{f=0}^{N/2} X[f] e^{2 pi i f n / N},
+    so 2 Re T[n] = x[n] + (X[0] + X[N/2] (-1)^n) / N -- checked against x."""
+    N = 512
+    g = O.geometry(64.0, N, (1.0,), 7.0, 7.0, 1, norm="none", window="tukey", window_param=0.0,
+                   stopband_eps=1.0, remodulate=True, n_out=N)
+    assert g.M == N and g.c[0, 0] == 1.0
+    x = _rand_x(N, 71) + 0.3            # a DC offset so the correction term matters
+    X = np.fft.rfft(x)
+    T = O.forward(g, x)[0, 0]
+    n = np.arange(N)
+    expect = 0.5 * (x + (X[0].real + X[-1].real * (-1.0) ** n) / N)
+    assert np.allclose(T.real, expect, rtol=0, atol=1e-13 * np.max(np.abs(x)))
