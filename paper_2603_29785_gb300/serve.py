@@ -96,6 +96,11 @@ class GpuExecutor(Executor):
         self.f_min, self.f_max = f_min, f_max
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
         self.ws = [None] * slots
+        # per-slot pinned staging (input samples, output samples or envelopes),
+        # grown on demand and reused: a slot's buffers are free again once its
+        # batch has been collected, and pinning per batch would cost milliseconds
+        self.pin_in = [None] * slots
+        self.pin_out = [None] * slots
         self.tune = tune
 
     def plan(self, fs, N, q):
@@ -121,17 +126,31 @@ class GpuExecutor(Executor):
             self.ws[slot] = ws
         return ws
 
+    def _pinned(self, pool, slot, shape, dtype):
+        """A pinned host tensor of `shape` and `dtype` on the slot's reusable bytes."""
+        t = self.torch
+        n = int(np.prod(shape)) * t.empty((), dtype=dtype).element_size()
+        buf = pool[slot]
+        if buf is None or buf.numel() < n:
+            buf = t.empty(max(n, 16), dtype=t.uint8).pin_memory()
+            pool[slot] = buf
+        return buf[:n].view(dtype).view(shape)
+
     def launch(self, batch, slot):
         from . import qtam
         t = self.torch
         fs, N, q, kind = batch.key
         p = self.plan(fs, N, q)
         st = self.streams[slot]
-        xs = np.concatenate([r.x for r in batch.requests]).astype(np.float32, copy=False)
-        B = xs.shape[0]
+        B = sum(r.x.shape[0] for r in batch.requests)
         dev = f"cuda:{self.device}"
+        x_host = self._pinned(self.pin_in, slot, (B, N), t.float32)
+        xs = x_host.numpy()
+        o = 0
+        for r in batch.requests:
+            xs[o:o + r.x.shape[0]] = r.x
+            o += r.x.shape[0]
         with t.cuda.stream(st):
-            x_host = t.from_numpy(xs).pin_memory()
             x = x_host.to(dev, non_blocking=True)
             y = p.envelope_tensor(B)
             ws = self._workspace(slot, qtam.qtam_workspace_size(p.handle, B))
@@ -143,13 +162,13 @@ class GpuExecutor(Executor):
                 qtam.qtam_scale_rows(p.handle, y, B, gain, st)
                 xh = t.empty((B, N), dtype=t.float32, device=dev)
                 qtam.qtam_inverse(p.handle, y, B, 0, xh, ws, ws.numel(), st)
-                out = t.empty((B, N), dtype=t.float32).pin_memory()
+                out = self._pinned(self.pin_out, slot, (B, N), t.float32)
                 out.copy_(xh, non_blocking=True)
-                keep = (x_host, gain, y, xh)
+                keep = (gain, y, xh)
             else:
-                out = t.empty(tuple(y.shape), dtype=y.dtype).pin_memory()
+                out = self._pinned(self.pin_out, slot, tuple(y.shape), y.dtype)
                 out.copy_(y, non_blocking=True)
-                keep = (x_host, x, y)
+                keep = (x, y)
             ev = t.cuda.Event()
             ev.record(st)
         batch.handle = (ev, out, keep)
