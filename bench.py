@@ -329,7 +329,10 @@ def run_gpu(args, rank, world, local):
         "path_hbm_frac": round(path_frac, 4),
         "stages": kernels,
         "e2e": e2e,
-        "gpu_launches": 7 * args.steps,
+        # per step: k_col_forward, k_row_forward, k_untangle_forward (spectrum), k_rows_forward_s
+        # (envelopes), k_rows_inverse_s (accumulate; the zeroing is a memset, not a kernel),
+        # k_untangle_inverse, k_row_inverse, k_col_inverse (synthesis) -- as the ncu launch list shows
+        "gpu_launches": 8 * args.steps,
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
