@@ -15,9 +15,16 @@
  *            F_tau = {P > 0, P >= tau max P}, 0 elsewhere; x_hat = irfft_N.
  *
  *   W_k[f] = c_k (1 - ((f - k_c)/h_k)^2)^2 on |f - k_c| <= h_k, 0 <= f <= N/2
- *            (Eq. gwpy_window_formula, Eq. support)
+ *            (Eq. gwpy_window_formula, Eq. support); the App. A alternatives
+ *            (Hann, Kaiser, Tukey, Planck-taper) per plan or per plane
  *   P[f]   = sum over the selected planes and rows of W_k[f]^2 (App. C frame
  *            operator), computed in FP64 on the host when the plan is made.
+ *
+ * Beyond the transform pair: per-plane energy / peak for optimal-plane
+ * selection, uneven batches, a host round trip with overlapped copies,
+ * overlap-save streaming over continuous signals, a dense (undemodulated,
+ * stopband-floored) mode with a single-tile inverse, and the short DFT on
+ * the tensor cores (tcgen05) for M = 8192.
  *
  * Conventions for every entry point:
  *  - Pointers named x, y, workspace are DEVICE pointers on the plan's device,
