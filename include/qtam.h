@@ -237,7 +237,8 @@ QTAM_API qtam_status qtam_inverse_single_tile(qtam_plan_t plan, const void* y, i
 /* Forward then inverse from HOST buffers: copies x_host into x_dev, runs
  * qtam_forward into y_dev and qtam_inverse into xhat_dev, and copies xhat_dev
  * back into xhat_host; synchronises `stream` before returning.  The batch is
- * split into chunks of about 16 MB of input (at most 8): host-to-device
+ * split into inner chunks of about 16 MB of input and short first and last
+ * chunks (about batch/16 segments; at most 10 chunks): host-to-device
  * copies run on one library-owned stream and device-to-host copies on
  * another, ordered against the transforms on `stream` by events, so the
  * copies of neighbouring chunks overlap the transforms (pinned host buffers

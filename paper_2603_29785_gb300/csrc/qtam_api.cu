@@ -1144,7 +1144,7 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
   DeviceGuard g(pl->device);
   std::lock_guard<std::mutex> lk(pl->rt_mu);
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  constexpr int kChunks = 8;
+  constexpr int kChunks = 10;
   cudaError_t e = cudaSuccess;
   if (!pl->rt_in) {
     e = cudaStreamCreateWithFlags(&pl->rt_in, cudaStreamNonBlocking);
@@ -1156,18 +1156,34 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
     }
     if (e != cudaSuccess) return fail_cuda(e, "round-trip streams");
   }
-  // chunk c of C holds segments [s0, s0 + nb); copies of neighbouring chunks
-  // overlap the transforms of chunk c on the caller's stream.  Chunks of about
-  // 16 MB of input: smaller ones expose less copy time at the ends but pay
-  // per-chunk launch and tail costs (measured best on the 64 s workload)
+  // chunk c holds segments [bound[c], bound[c + 1]); copies of neighbouring
+  // chunks overlap the transforms of chunk c on the caller's stream.  Inner
+  // chunks carry about 16 MB of input (smaller ones pay per-chunk launch and
+  // tail costs; measured best on the 64 s workload); the first and last
+  // chunks are cut to about B/16 segments, since their copies cannot overlap
+  // anything
   const size_t xs = (size_t)pl->N * pl->real_size();
-  const int64_t by_bytes = (int64_t)((size_t)B * xs / (16u << 20));
-  const int C = (int)std::max<int64_t>(1, std::min<int64_t>({B, (int64_t)kChunks, by_bytes}));
+  std::vector<int64_t> bound{0};
+  {
+    const int64_t by_bytes = (int64_t)((size_t)B * xs / (16u << 20));
+    if (by_bytes < 2) {
+      bound.push_back(B);
+    } else {
+      const int64_t edge = std::max<int64_t>(1, B / 16);
+      const int64_t inner = B - 2 * edge;
+      const int64_t ni = std::max<int64_t>(
+          1, std::min<int64_t>({(int64_t)kChunks - 2, inner, (int64_t)((size_t)inner * xs / (16u << 20))}));
+      bound.push_back(edge);
+      for (int64_t i = 1; i <= ni; ++i) bound.push_back(edge + inner * i / ni);
+      bound.push_back(B);
+    }
+  }
+  const int C = (int)bound.size() - 1;
   const size_t ys = (size_t)pl->P * pl->K * pl->M * pl->env_size();
   cudaEvent_t ev_start = pl->rt_ev[0], ev_end = pl->rt_ev[1];
   cudaEvent_t* ev_in = &pl->rt_ev[2];
   cudaEvent_t* ev_done = &pl->rt_ev[2 + kChunks];
-  auto seg0 = [&](int c) { return (int64_t)c * (B / C) + std::min<int64_t>(c, B % C); };
+  auto seg0 = [&](int c) { return bound[c]; };
   if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess) return fail_cuda(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(pl->rt_in, ev_start, 0)) != cudaSuccess ||
       (e = cudaStreamWaitEvent(pl->rt_out, ev_start, 0)) != cudaSuccess)
