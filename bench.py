@@ -680,8 +680,9 @@ def run_precision(args, local):
     """Precision sweep on the 64 s workload: envelope storage FP32 / BF16 / FP16
     at M = 4800 (CUDA-core FFTs), and at M = 8192 the CUDA-core runtime engine
     against the tensor-core short DFT (64 x 128 four-step on tcgen05, BF16
-    operands): error against the FP64 oracle (2 segments), fwd+inv throughput
-    and the envelope stage alone (64 segments)."""
+    operands, both directions): error against the FP64 oracle (2 segments),
+    fwd+inv throughput, and the envelope and accumulation stages alone (64
+    segments)."""
     import torch
     from oracle import qtam_oracle as O
     from paper_2603_29785_gb300 import qtam, tune as qtune
@@ -718,7 +719,7 @@ def run_precision(args, local):
         rr = refs[n_out]
         ef = max(float(np.linalg.norm(yv[b] - rr[b][0]) / np.linalg.norm(rr[b][0])) for b in range(2))
         er = max(float(np.linalg.norm(xh[b].cpu().numpy() - rr[b][1]) / np.linalg.norm(rr[b][1])) for b in range(2))
-        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
         for _ in range(3):
             p.forward(x, y); p.inverse(y, x=xh)
         e[0].record(st)
@@ -735,17 +736,27 @@ def run_precision(args, local):
         e[3].record(st)
         e[3].synchronize()
         ms_env = e[2].elapsed_time(e[3]) / args.steps
+        A = p.accumulate(y)
+        e[4].record(st)
+        for _ in range(args.steps):
+            qtam.qtam_stage_accumulate(p.handle, y, B, 0, A, st)
+        e[5].record(st)
+        e[5].synchronize()
+        ms_acc = e[4].elapsed_time(e[5]) / args.steps
         item = {"envelope": env, "M": p.M, "short_dft": sd, "forward_rel_err": ef, "roundtrip_rel_err": er,
                 "msamples_per_s": round(B * W["N"] / ms / 1e3, 1), "ms_per_step": round(ms, 4),
-                "envelope_stage_ms": round(ms_env, 4),
+                "envelope_stage_ms": round(ms_env, 4), "accumulate_stage_ms": round(ms_acc, 4),
                 "envelope_stage_GB_s": round(B * p.info["envelope_bytes_per_segment"] / (ms_env * 1e-3) / 1e9, 1),
                 "envelope_bytes_per_segment": p.info["envelope_bytes_per_segment"]}
         if sd == "tensor":
-            # two tcgen05 GEMMs per pair of rows: 128x256x128 + 4 x 128x128x128 multiply-adds
+            # two tcgen05 GEMMs per pair of rows in each direction: 128x256x128 +
+            # 4 x 128x128x128 multiply-adds
             flops = B * p.P * p.K / 2 * 2 * (128 * 256 * 128 + 4 * 128 * 128 * 128)
             tf = flops / (ms_env * 1e-3) / 1e12
+            tfi = flops / (ms_acc * 1e-3) / 1e12
             pk = float(peaks.get("bf16_tflops", 1900.0))
             item["tensor"] = {"achieved_tflops": round(tf, 1), "peak_tflops": pk, "frac": round(tf / pk, 4),
+                              "inverse_achieved_tflops": round(tfi, 1), "inverse_frac": round(tfi / pk, 4),
                               "peak_source": "measured" if "bf16_tflops" in peaks else "fallback"}
         out.append(item)
     line = {"metric": "QTAM precision sweep: error vs FP64 oracle and Msamples/s per envelope dtype and short-DFT engine",

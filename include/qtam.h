@@ -118,8 +118,10 @@ typedef struct {
    * length-8192 DFT as a 64 x 128 four-step whose two DFT stages are BF16
    * matrix products on the tensor cores with FP32 accumulation and an FP32
    * twiddle between them; needs n_out = 8192 and F32 compute, else
-   * QTAM_ERR_UNSUPPORTED_SIZE).  Its envelopes carry BF16 operand rounding
-   * (relative error ~1e-3); the inverse stays on the CUDA cores. */
+   * QTAM_ERR_UNSUPPORTED_SIZE).  The inverse runs the mirrored four-step
+   * (DFT-128 then twiddle then DFT-64, on the tensor cores) when the
+   * envelope pointer is 16-byte aligned, else the CUDA-core rows.  Both
+   * directions carry BF16 operand rounding (relative error ~3e-3). */
   int32_t short_dft;
   /* dense mode (NEXT to the demodulated default; Sec. III alternative
    * inversion): stopband_eps > 0 gives every window the floor eps wherever it
@@ -154,7 +156,8 @@ typedef struct {
   int64_t kept_bins;              /* |F_tau| for all planes */
   int64_t device_bytes;           /* bytes of resident plan tables on the device */
   int32_t row_variant;            /* CUDA-core row-kernel variant in use (-1: runtime engine); with
-                                     the tensor-core short DFT it serves the inverse only */
+                                     the tensor-core short DFT it serves only an inverse of
+                                     envelopes that are not 16-byte aligned */
   int32_t short_dft;              /* QTAM_SHORT_DFT_* engine of the envelope stage */
 } qtam_plan_info_t;
 

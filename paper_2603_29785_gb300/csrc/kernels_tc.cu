@@ -1,6 +1,6 @@
 // Tensor-core (tcgen05) kernels: a BF16 GEMM tile check that exercises the
 // descriptors, tensor-memory allocation, MMA, commit and loads on their own,
-// and the tensor-core short DFT of the row kernels.
+// and the tensor-core short DFT of the forward and inverse row kernels.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
@@ -365,6 +365,350 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (warp == 0) tc::tmem_dealloc(tbase, 512);
 }
 
+// ---- tensor-core analysis DFT of the inverse rows (M = 8192) -----------------
+//
+// Inverse rows (steps b1-b2), two rows per CTA iteration.  The synthesis
+// needs S[j] = sum_n y[n] e^{-2 pi i j n/8192} of each envelope row; with
+// n = n1 + 64 n2 and j = 128 j1 + j2 it factors into
+//   E[n1][j2]      = sum_n2 y[n1 + 64 n2] e^{-2 pi i j2 n2/128}   GEMM B' (tensor cores)
+//   E'[n1][j2]     = E[n1][j2] e^{-2 pi i j2 n1/8192}             twiddle (FP32)
+//   S[128 j1 + j2] = sum_n1 E'[n1][j2] e^{-2 pi i j1 n1/64}       GEMM A' (tensor cores)
+// and the band accumulation A[k_c + d] += c_k sqrt(N/M) W'(d) S[d mod M] for
+// |d| <= h (the weight c_inv W').
+//   GEMM B' (the pair): M = 128 rows (64 r + n1), K = 128 + 128 (Re y, Im y
+//           over n2), N = 128 + 128: Re E = Re y Gr + Im y Gi, Im E = Im y Gr
+//           - Re y Gi (the minus sign through the negate-A bit).  The
+//           envelopes are the M-major A operand: 8 consecutive samples n1 of
+//           one n2 fill one 16-byte row of a core matrix.
+//   GEMM A' (per row r): M = 128 (j2), K = 128 (Re E', Im E' over n1), N =
+//           128 (Re S, Im S over j1); E'^T is the M-major A operand written
+//           by the twiddle pass, B the conjugate DFT-64 block matrix.  A lane
+//           of the result holds S at bins j2 + 128 j1, so a warp's reductions
+//           go to 32 consecutive bins.
+// Shared memory: conjugate DFT-64 block 32 KB, Gr 32 KB, Gi 32 KB, 64 KB for
+// the next pair's envelopes, 64 KB for E'^T.  Tensor memory: S of row r in
+// 128 r .. 128 r + 127, E in 256..511.
+// Pipeline per pair i: GEMM B'(i) runs while the CUDA cores accumulate pair
+// i-1 from the S columns; GEMM A'(i) runs while they store pair i+1's
+// envelopes into sY, whose loads were issued under the earlier phases.
+
+// 8 consecutive complex envelope samples (16-byte aligned): load() issues the
+// 16-byte loads, pack() turns them into 8 BF16 real parts and 8 BF16
+// imaginary parts, packed in order
+template <int E> struct TcLoad;
+template <> struct TcLoad<ENV_F32> {
+  struct Raw { float4 v[4]; };
+  __device__ static void load(const float2* p, Raw& w) {
+    const float4* q = reinterpret_cast<const float4*>(p);
+#pragma unroll
+    for (int t = 0; t < 4; ++t) w.v[t] = __ldcs(q + t);
+  }
+  __device__ static void pack(const Raw& w, uint4& re, uint4& im) {
+    re = make_uint4(pack_bf16(w.v[0].x, w.v[0].z), pack_bf16(w.v[1].x, w.v[1].z), pack_bf16(w.v[2].x, w.v[2].z),
+                    pack_bf16(w.v[3].x, w.v[3].z));
+    im = make_uint4(pack_bf16(w.v[0].y, w.v[0].w), pack_bf16(w.v[1].y, w.v[1].w), pack_bf16(w.v[2].y, w.v[2].w),
+                    pack_bf16(w.v[3].y, w.v[3].w));
+  }
+};
+template <> struct TcLoad<ENV_BF16> {   // already BF16: regroup the halves, no rounding
+  struct Raw { uint4 v[2]; };
+  __device__ static void load(const __nv_bfloat162* p, Raw& w) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    w.v[0] = __ldcs(q);
+    w.v[1] = __ldcs(q + 1);
+  }
+  __device__ static void pack(const Raw& w, uint4& re, uint4& im) {
+    const uint4 a = w.v[0], b = w.v[1];
+    re = make_uint4(__byte_perm(a.x, a.y, 0x5410), __byte_perm(a.z, a.w, 0x5410), __byte_perm(b.x, b.y, 0x5410),
+                    __byte_perm(b.z, b.w, 0x5410));
+    im = make_uint4(__byte_perm(a.x, a.y, 0x7632), __byte_perm(a.z, a.w, 0x7632), __byte_perm(b.x, b.y, 0x7632),
+                    __byte_perm(b.z, b.w, 0x7632));
+  }
+};
+template <> struct TcLoad<ENV_F16> {
+  struct Raw { uint4 v[2]; };
+  __device__ static void load(const __half2* p, Raw& w) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+    w.v[0] = __ldcs(q);
+    w.v[1] = __ldcs(q + 1);
+  }
+  __device__ static void pack(const Raw& w, uint4& re, uint4& im) {
+    const uint32_t u[8] = {w.v[0].x, w.v[0].y, w.v[0].z, w.v[0].w, w.v[1].x, w.v[1].y, w.v[1].z, w.v[1].w};
+    uint32_t rr[4], ii[4];
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const float2 a = __half22float2(*reinterpret_cast<const __half2*>(&u[2 * t]));
+      const float2 b = __half22float2(*reinterpret_cast<const __half2*>(&u[2 * t + 1]));
+      rr[t] = pack_bf16(a.x, b.x);
+      ii[t] = pack_bf16(a.y, b.y);
+    }
+    re = make_uint4(rr[0], rr[1], rr[2], rr[3]);
+    im = make_uint4(ii[0], ii[1], ii[2], ii[3]);
+  }
+};
+
+// *p += v when `on` (one predicated vector reduction; A is not read here)
+__device__ __forceinline__ void red_add_if(float2* p, float v0, float v1, bool on) {
+  asm volatile("{ .reg .pred q; setp.ne.b32 q, %3, 0; @q red.global.add.v2.f32 [%0], {%1, %2}; }" ::"l"(p), "f"(v0),
+               "f"(v1), "r"((int)on));
+}
+
+// Envelopes of pair pr into sY ([128 m = 64 r + n1][256 k = Re n2 | Im n2],
+// M-major), one row r at a time: tc_load_row issues the loads into
+// registers, tc_store_row packs and stores them, so the loads can be in
+// flight while other work runs.  Item (r, n2, octet o) holds samples 8 o +
+// 64 n2 .. + 7; the 8 lanes of a quarter warp take 8 consecutive n2 of one
+// octet, so their 16-byte stores fill one core matrix (no bank conflicts)
+// and each lane reads whole 32-byte sectors.
+template <int E>
+__device__ __forceinline__ const typename TcEnv<E>::S* tc_row_ptr(int64_t pr, int r, int64_t n_units, int n_sel,
+                                                                 int n_rows, const int* __restrict__ row_list,
+                                                                 const typename TcEnv<E>::S* __restrict__ y) {
+  const int64_t u = 2 * pr + r;
+  if (u >= n_units) return nullptr;
+  const int64_t seg = u / n_sel;
+  return y + (seg * n_rows + row_list[u - seg * n_sel]) * (int64_t)kTcM;
+}
+
+template <int E>
+__device__ __forceinline__ void tc_load_row(const typename TcEnv<E>::S* yr, typename TcLoad<E>::Raw (&raw)[2]) {
+  if (!yr) return;
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int i = threadIdx.x + kTcThreads * t;   // 0 .. 1023
+    TcLoad<E>::load(yr + 8 * ((i >> 3) & 7) + 64 * ((i & 7) + 8 * (i >> 6)), raw[t]);
+  }
+}
+
+template <int E>
+__device__ __forceinline__ void tc_store_row(unsigned char* sY, int r, bool valid,
+                                             const typename TcLoad<E>::Raw (&raw)[2]) {
+#pragma unroll
+  for (int t = 0; t < 2; ++t) {
+    const int i = threadIdx.x + kTcThreads * t;
+    const int n2 = (i & 7) + 8 * (i >> 6), o = (i >> 3) & 7;
+    uint4 re = make_uint4(0u, 0u, 0u, 0u), im = re;
+    if (valid) TcLoad<E>::pack(raw[t], re, im);
+    const int m = 64 * r + 8 * o;
+    *reinterpret_cast<uint4*>(sY + tc::cm_offset_mn(m, n2, 256)) = re;
+    *reinterpret_cast<uint4*>(sY + tc::cm_offset_mn(m, 128 + n2, 256)) = im;
+  }
+}
+
+// Band accumulation of pair pr from tensor memory (S of row r in columns
+// 128 r: Re over j1, 128 r + 64: Im).  Warp (q4, quarter) reads lanes j2 =
+// 32 q4 + lane of row r = quarter >> 1, j1 in 32 (quarter & 1) .. + 31;
+// blocks of 16 j1 wholly outside the band are skipped by the whole warp.
+__device__ __forceinline__ void tc_accumulate(uint32_t tbase, int64_t pr, int64_t n_units, int n_sel,
+                                              const int* __restrict__ row_list, const RowDev<float>* __restrict__ rows,
+                                              int64_t Nr, float2* __restrict__ A, const float* __restrict__ wtab) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int q4 = warp & 3, quarter = warp >> 2;
+  const int r = quarter >> 1, jb = 32 * (quarter & 1), j2 = 32 * q4 + lane;
+  const int64_t u = 2 * pr + r;
+  if (u >= n_units) return;   // r is uniform per warp
+  const int64_t seg = u / n_sel;
+  const RowDev<float> rd = rows[row_list[u - seg * n_sel]];
+  const int dhi = (int)min((int64_t)rd.h, Nr - 1 - rd.kc);
+  const int mlo = kTcM + max(-rd.h, -rd.kc);
+  float2* As = A + seg * Nr + rd.kc;
+  const bool tab = wtab != nullptr && rd.woff >= 0;
+  const float h2 = (float)rd.h * (float)rd.h;   // exact: h < 4096
+  const uint32_t lrow = (uint32_t)(32 * q4) << 16;
+#pragma unroll 1
+  for (int q = 0; q < 2; ++q) {
+    const int j10 = jb + 16 * q;
+    if (!(128 * j10 + 32 * q4 <= dhi || 128 * (j10 + 15) + 32 * q4 + 31 >= mlo)) continue;
+    float vr[16], vi[16];
+    tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(128 * r + j10), vr);
+    tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(128 * r + 64 + j10), vi);
+    tc::tmem_wait_ld(vr, vi);
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const int j = 128 * (j10 + e) + j2;
+      const bool lo = j <= dhi, hi = j >= mlo;
+      const int d = lo ? j : j - kTcM;
+      float w;
+      if (tab) {
+        w = rd.c_inv * wtab[rd.woff + min(d < 0 ? -d : d, rd.h)];
+      } else {
+        const float df = (float)d;
+        const float t = (h2 - df * df) * rd.kw_inv;
+        w = t * t;
+      }
+      red_add_if(As + d, vr[e] * w, vi[e] * w, lo || hi);
+    }
+  }
+}
+
+template <int E>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_rows_inverse_tc(const RowDev<float>* __restrict__ rows, const int* __restrict__ row_list, int n_sel, int n_rows,
+                      int64_t Nr, const typename TcEnv<E>::S* __restrict__ y, float2* __restrict__ A, int64_t n_units,
+                      const uint4* __restrict__ tabAi, const uint4* __restrict__ tabG, const float* __restrict__ wtab) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  __shared__ __align__(8) uint64_t mbarA, mbarB;
+  __shared__ uint32_t tslot;
+  __shared__ int abort_flag;
+  unsigned char* sAi = sm;            // conjugate DFT-64 block, [128 n][128 k] K-major (GEMM A''s B)
+  unsigned char* sGr = sm + 32768;    // [128 j2][128 n2]
+  unsigned char* sGi = sm + 65536;
+  unsigned char* sY = sm + 98304;     // envelopes of the next pair, [128 m][256 k] M-major
+  unsigned char* sE = sm + 163840;    // E'^T of the current pair: row r at 32 KB r, [128 j2][128 k] M-major
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  for (int i = tid; i < 2048; i += kTcThreads) reinterpret_cast<uint4*>(sAi)[i] = tabAi[i];
+  for (int i = tid; i < 4096; i += kTcThreads) reinterpret_cast<uint4*>(sGr)[i] = tabG[i];
+  if (warp == 0) {
+    tc::tmem_alloc(&tslot, 512);
+    tc::tmem_relinquish();
+  }
+  if (tid == 0) {
+    tc::mbar_init(&mbarA, 1);
+    tc::mbar_init(&mbarB, 1);
+    abort_flag = 0;
+  }
+  // twiddle pass: warp (q4, cg) takes lanes m = 32 q4 + lane = 64 r + n1 and
+  // columns j2 in 32 cg .. 32 cg + 31; e^{-2 pi i n1 j2 / 8192} from the
+  // exact integer n1 j2 with the SFU sine/cosine
+  const int q4 = warp & 3, cg = warp >> 2;
+  const int m = 32 * q4 + lane, rr = m >> 6, n1 = m & 63;
+  constexpr float kAng = 6.28318530717958647692f / (float)kTcM;
+  const int64_t n_pairs = (n_units + 1) >> 1;
+  int64_t pr = blockIdx.x;
+  typename TcLoad<E>::Raw raw[2];
+  if (pr < n_pairs) {
+#pragma unroll 1
+    for (int r = 0; r < 2; ++r) {
+      const typename TcEnv<E>::S* yr = tc_row_ptr<E>(pr, r, n_units, n_sel, n_rows, row_list, y);
+      tc_load_row<E>(yr, raw);
+      tc_store_row<E>(sY, r, yr != nullptr, raw);
+    }
+  }
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tbase = tslot;
+  const uint32_t aAi = tc::smem_addr(sAi), aGr = tc::smem_addr(sGr), aGi = tc::smem_addr(sGi);
+  const uint32_t aY = tc::smem_addr(sY), aE = tc::smem_addr(sE);
+  uint32_t phA = 0, phB = 0;
+  bool pendA = false, pendB = false;
+  int64_t prev = -1;
+
+  for (; pr < n_pairs; pr += gridDim.x) {
+    // ---- GEMM B': Re E [tmem 256..383], Im E [384..511] ----
+    if (tid == 0) {
+      const uint32_t id = tc::make_idesc_bf16(128, 128, false, false, true),
+                     idn = tc::make_idesc_bf16(128, 128, true, false, true);   // y is M-major
+      const uint32_t tRe = tbase + 256u, tIm = tbase + 384u;
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {   // + Re y * Gr, - Re y * Gi
+        const uint64_t a = tc::make_sdesc(aY + 256u * s, 128u, 4096u);
+        tc::mma_bf16(tRe, a, tc::make_sdesc(aGr + 256u * s, 128u, 2048u), id, s > 0);
+        tc::mma_bf16(tIm, a, tc::make_sdesc(aGi + 256u * s, 128u, 2048u), idn, s > 0);
+      }
+#pragma unroll
+      for (int s = 0; s < 8; ++s) {   // + Im y * Gi, + Im y * Gr
+        const uint64_t a = tc::make_sdesc(aY + 256u * (8 + s), 128u, 4096u);
+        tc::mma_bf16(tRe, a, tc::make_sdesc(aGi + 256u * s, 128u, 2048u), id, 1u);
+        tc::mma_bf16(tIm, a, tc::make_sdesc(aGr + 256u * s, 128u, 2048u), id, 1u);
+      }
+      tc::mma_commit(&mbarB);
+    }
+    pendB = true;
+    // The next pair's envelopes are loaded a row at a time, each row's loads
+    // in flight under other work (all CTAs would otherwise load at once and
+    // leave the memory idle between bursts): row 0 under the accumulation
+    // below, stored once GEMM B' has released sY; row 1 under the twiddle,
+    // stored under GEMM A'.
+    const int64_t nx = pr + gridDim.x;
+    const typename TcEnv<E>::S* ynx0 =
+        nx < n_pairs ? tc_row_ptr<E>(nx, 0, n_units, n_sel, n_rows, row_list, y) : nullptr;
+    const typename TcEnv<E>::S* ynx1 =
+        nx < n_pairs ? tc_row_ptr<E>(nx, 1, n_units, n_sel, n_rows, row_list, y) : nullptr;
+    tc_load_row<E>(ynx0, raw);
+    // ... overlapped with the previous pair's band accumulation (S columns are not touched by GEMM B')
+    if (prev >= 0) tc_accumulate(tbase, prev, n_units, n_sel, row_list, rows, Nr, A, wtab);
+    if (!tc::mbar_wait_bounded(&mbarB, phB, tc::kWaitCycles)) abort_flag = 1;
+    tc::fence_after_sync();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (abort_flag) break;
+    phB ^= 1u;
+    pendB = false;
+    if (nx < n_pairs) tc_store_row<E>(sY, 0, ynx0 != nullptr, raw);
+    tc_load_row<E>(ynx1, raw);
+    // ---- twiddle: E -> E'^T (row rr at 32 KB rr, [128 j2][128 k = Re n1 | Im n1], M-major) ----
+    {
+      const uint32_t lrow = (uint32_t)(32 * q4) << 16;
+      unsigned char* sEr = sE + 32768 * rr;
+#pragma unroll 1
+      for (int h = 0; h < 2; ++h) {
+        const int j20 = 32 * cg + 16 * h;
+        float vr[16], vi[16];
+        tc::tmem_ld16_nowait(tbase + lrow + 256u + (uint32_t)j20, vr);
+        tc::tmem_ld16_nowait(tbase + lrow + 384u + (uint32_t)j20, vi);
+        tc::tmem_wait_ld(vr, vi);
+        float orr[16], oi[16];
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          float ts, tcs;
+          __sincosf(kAng * (float)(n1 * (j20 + e)), &ts, &tcs);
+          orr[e] = fmaf(vr[e], tcs, vi[e] * ts);
+          oi[e] = fmaf(vi[e], tcs, -vr[e] * ts);
+        }
+#pragma unroll
+        for (int g = 0; g < 2; ++g) {
+          const int jg = j20 + 8 * g;
+          *reinterpret_cast<uint4*>(sEr + tc::cm_offset_mn(jg, n1, 128)) =
+              make_uint4(pack_bf16(orr[8 * g], orr[8 * g + 1]), pack_bf16(orr[8 * g + 2], orr[8 * g + 3]),
+                         pack_bf16(orr[8 * g + 4], orr[8 * g + 5]), pack_bf16(orr[8 * g + 6], orr[8 * g + 7]));
+          *reinterpret_cast<uint4*>(sEr + tc::cm_offset_mn(jg, 64 + n1, 128)) =
+              make_uint4(pack_bf16(oi[8 * g], oi[8 * g + 1]), pack_bf16(oi[8 * g + 2], oi[8 * g + 3]),
+                         pack_bf16(oi[8 * g + 4], oi[8 * g + 5]), pack_bf16(oi[8 * g + 6], oi[8 * g + 7]));
+        }
+      }
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    // ---- GEMM A': S_r [tmem 128 r ..] = E'_r^T * conj(DFT64)^T, r = 0, 1 ----
+    if (tid == 0) {
+      const uint32_t idesc = tc::make_idesc_bf16(128, 128, false, false, true);   // E'^T is M-major
+#pragma unroll
+      for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int s = 0; s < 8; ++s)
+          tc::mma_bf16(tbase + 128u * r, tc::make_sdesc(aE + 32768u * r + 256u * s, 128u, 2048u),
+                       tc::make_sdesc(aAi + 256u * s, 128u, 2048u), idesc, s > 0);
+      tc::mma_commit(&mbarA);
+    }
+    pendA = true;
+    // ... overlapped with the store of the next pair's row 1 (GEMM B' has finished reading sY)
+    if (nx < n_pairs) tc_store_row<E>(sY, 1, ynx1 != nullptr, raw);
+    if (!tc::mbar_wait_bounded(&mbarA, phA, tc::kWaitCycles)) abort_flag = 1;
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    if (abort_flag) break;
+    phA ^= 1u;
+    pendA = false;
+    prev = pr;
+  }
+  if (!abort_flag && prev >= 0) tc_accumulate(tbase, prev, n_units, n_sel, row_list, rows, Nr, A, wtab);
+  if (abort_flag) {
+    if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
+    if (pendA) tc::mbar_wait_bounded(&mbarA, phA, tc::kWaitCycles);
+    if (pendB) tc::mbar_wait_bounded(&mbarB, phB, tc::kWaitCycles);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tbase, 512);
+}
+
 }  // namespace
 
 bool tc_forward_supported(int M) { return M == kTcM; }
@@ -398,6 +742,45 @@ cudaError_t launch_rows_forward_tc(const RowCfg& c, const RowDev<float>* rows, i
                                                                     units, A, G, wtab);
   }
   return cudaGetLastError();
+}
+
+
+bool launch_rows_inverse_tc(const RowCfg& c, const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows,
+                            int64_t Nr, const void* y, int env, float2* A, int64_t B, cudaStream_t st,
+                            const float* wtab, cudaError_t* err) {
+  *err = cudaSuccess;
+  if (!c.tcAi || (reinterpret_cast<uintptr_t>(y) & 15)) return false;   // 16-byte envelope loads
+  const int64_t units = B * n_sel;
+  if (units == 0) return true;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t pairs = (units + 1) / 2;
+  const unsigned grid = (unsigned)std::min<int64_t>(pairs, (int64_t)std::max(sms, 1));
+  const uint4* Ai = static_cast<const uint4*>(c.tcAi);
+  const uint4* G = static_cast<const uint4*>(c.tcG);
+  cudaError_t e;
+  switch (env) {
+    case ENV_BF16:
+      if ((e = allow_smem((const void*)k_rows_inverse_tc<ENV_BF16>, kTcSmem)) != cudaSuccess) break;
+      k_rows_inverse_tc<ENV_BF16><<<grid, kTcThreads, kTcSmem, st>>>(
+          rows, row_list, n_sel, n_rows, Nr, static_cast<const __nv_bfloat162*>(y), A, units, Ai, G, wtab);
+      e = cudaGetLastError();
+      break;
+    case ENV_F16:
+      if ((e = allow_smem((const void*)k_rows_inverse_tc<ENV_F16>, kTcSmem)) != cudaSuccess) break;
+      k_rows_inverse_tc<ENV_F16><<<grid, kTcThreads, kTcSmem, st>>>(
+          rows, row_list, n_sel, n_rows, Nr, static_cast<const __half2*>(y), A, units, Ai, G, wtab);
+      e = cudaGetLastError();
+      break;
+    default:
+      if ((e = allow_smem((const void*)k_rows_inverse_tc<ENV_F32>, kTcSmem)) != cudaSuccess) break;
+      k_rows_inverse_tc<ENV_F32><<<grid, kTcThreads, kTcSmem, st>>>(
+          rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, Ai, G, wtab);
+      e = cudaGetLastError();
+  }
+  *err = e;
+  return true;
 }
 
 }  // namespace qtam

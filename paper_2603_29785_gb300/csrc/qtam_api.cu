@@ -198,7 +198,8 @@ struct qtam_plan_s {
   void* d_twN = nullptr;
   void* d_tw4 = nullptr;
   void* d_wtab = nullptr;   // W'(0..h) per distinct half-width, non-bisquare windows only
-  void* d_tcA = nullptr;    // tensor-core short DFT operands and twiddles (short_dft = TENSOR)
+  void* d_tcA = nullptr;    // tensor-core short DFT operands (short_dft = TENSOR)
+  void* d_tcAi = nullptr;
   void* d_tcG = nullptr;
   void* d_ones = nullptr;   // dense mode: 1/P := 1 for the single-tile inverse
   size_t device_bytes = 0;
@@ -392,16 +393,20 @@ uint16_t to_bf16(double x) {
 //  A: DFT-64 block matrix as GEMM A's B operand, row n1 (Re D) or 64 + n1
 //     (Im D), column j1 (times Re Z) or 64 + j1 (times Im Z):
 //     [cos, -sin; sin, cos] of 2 pi j1 n1 / 64;
+//  Ai: the conjugate block matrix as the inverse GEMM A''s B operand, row j1
+//     (Re S) or 64 + j1 (Im S), column n1 (times Re E') or 64 + n1 (Im E'):
+//     [cos, sin; -sin, cos] of 2 pi j1 n1 / 64;
 //  G: cosine then sine DFT-128 matrices [n2][j2] of 2 pi j2 n2 / 128.
 qtam_status upload_tc_tables(qtam_plan_s* pl, size_t& tot) {
   const double two_pi = 6.283185307179586476925286766559;
-  std::vector<uint16_t> A(128 * 128), G(2 * 128 * 128);
+  std::vector<uint16_t> A(128 * 128), Ai(128 * 128), G(2 * 128 * 128);
   for (int c = 0; c < 128; ++c)
     for (int k = 0; k < 128; ++k) {
-      const int n1 = c & 63, part = c >> 6, j1 = k & 63, comp = k >> 6;
-      const double th = two_pi * (double)((j1 * n1) % 64) / 64.0;
-      const double v = part == 0 ? (comp == 0 ? std::cos(th) : -std::sin(th)) : (comp == 0 ? std::sin(th) : std::cos(th));
-      A[qtam::tc::cm_offset(c, k, 128) / 2] = to_bf16(v);
+      const int a = c & 63, part = c >> 6, b = k & 63, comp = k >> 6;
+      const double th = two_pi * (double)((a * b) % 64) / 64.0;
+      const double co = std::cos(th), si = std::sin(th);
+      A[qtam::tc::cm_offset(c, k, 128) / 2] = to_bf16(part == 0 ? (comp == 0 ? co : -si) : (comp == 0 ? si : co));
+      Ai[qtam::tc::cm_offset(c, k, 128) / 2] = to_bf16(part == 0 ? (comp == 0 ? co : si) : (comp == 0 ? -si : co));
     }
   for (int n2 = 0; n2 < 128; ++n2)
     for (int j2 = 0; j2 < 128; ++j2) {
@@ -411,8 +416,10 @@ qtam_status upload_tc_tables(qtam_plan_s* pl, size_t& tot) {
     }
   qtam_status s;
   if ((s = upload(&pl->d_tcA, A.data(), A.size() * 2, tot)) != QTAM_OK) return s;
+  if ((s = upload(&pl->d_tcAi, Ai.data(), Ai.size() * 2, tot)) != QTAM_OK) return s;
   if ((s = upload(&pl->d_tcG, G.data(), G.size() * 2, tot)) != QTAM_OK) return s;
   pl->rc.tcA = pl->d_tcA;
+  pl->rc.tcAi = pl->d_tcAi;
   pl->rc.tcG = pl->d_tcG;
   return QTAM_OK;
 }
@@ -526,6 +533,7 @@ void free_plan(qtam_plan_s* pl) {
     cudaFree(pl->d_tw4);
     cudaFree(pl->d_wtab);
     cudaFree(pl->d_tcA);
+    cudaFree(pl->d_tcAi);
     cudaFree(pl->d_tcG);
     cudaFree(pl->d_ones);
     cudaFree(pl->d_stw_col);
@@ -606,6 +614,13 @@ qtam_status run_accumulate(qtam_plan_s* pl, const void* y, int64_t B, const Mask
   using V = cplx<T>;
   cudaError_t e = cudaMemsetAsync(A, 0, (size_t)B * pl->Nr * sizeof(V), st);
   if (e != cudaSuccess) return fail_cuda(e, "cudaMemsetAsync");
+  if constexpr (sizeof(T) == 4) {
+    if (pl->rc.tensor &&
+        launch_rows_inverse_tc(pl->rc, static_cast<const RowDev<float>*>(pl->d_rows), me->rows, me->n_sel,
+                               pl->P * pl->K, pl->Nr, y, pl->env, static_cast<float2*>(A), B, st,
+                               static_cast<const float*>(pl->d_wtab), &e))
+      return e == cudaSuccess ? QTAM_OK : fail_cuda(e, "tensor-core accumulate");
+  }
   e = launch_rows_inverse<T>(pl->rc, static_cast<const RowDev<T>*>(pl->d_rows), me->rows, me->n_sel, pl->P * pl->K,
                              pl->Nr, y, pl->env, static_cast<V*>(A), B, static_cast<const V*>(pl->d_twM), st,
                              static_cast<const T*>(pl->d_wtab));

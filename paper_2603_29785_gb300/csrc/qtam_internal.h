@@ -68,19 +68,27 @@ struct RowCfg {
   int variant;   // index of a compile-time row-kernel variant, -1 = runtime engine
   int remod = 0; // dense mode: remodulated envelopes (runtime engine only)
   const void* stw = nullptr;   // stage twiddle tables of that variant
-  // tensor-core short DFT (M = 8192): DFT-64 block operand, DFT-128 cosine
-  // and sine operands; used when `tensor` is set
+  // tensor-core short DFT (M = 8192): DFT-64 block operand, its conjugate
+  // transpose (the inverse rows), DFT-128 cosine and sine operands; used
+  // when `tensor` is set
   int tensor = 0;
   const void* tcA = nullptr;
+  const void* tcAi = nullptr;
   const void* tcG = nullptr;
 };
 
 enum EnvKind { ENV_F32 = 0, ENV_F64 = 1, ENV_BF16 = 2, ENV_F16 = 3 };
 
-// Tensor-core forward rows (kernels_tc.cu): M must be 8192, FP32 compute.
+// Tensor-core rows (kernels_tc.cu): M must be 8192, FP32 compute.
 bool tc_forward_supported(int M);
 cudaError_t launch_rows_forward_tc(const RowCfg& c, const RowDev<float>* rows, int n_rows, int64_t Nr,
                                    const float2* X, void* y, int env, int64_t B, cudaStream_t st, const float* wtab);
+// Tensor-core inverse rows (accumulate into A, zeroed by the caller).  False
+// (nothing launched) when y is not 16-byte aligned: the CUDA-core rows then
+// serve; otherwise *err holds the launch status.
+bool launch_rows_inverse_tc(const RowCfg& c, const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows,
+                            int64_t Nr, const void* y, int env, float2* A, int64_t B, cudaStream_t st,
+                            const float* wtab, cudaError_t* err);
 
 // A compile-time row-kernel variant (FP32 compute): fixed M, radix sequence,
 // rows per block and occupancy target.  fwd/inv are indexed by EnvKind.
