@@ -543,15 +543,19 @@ def run_stream(args, local):
 def run_dense(args, local):
     """Dense mode: 2 s @ 4096 Hz segments (N = 8192), Q {4,8,16} x 64 rows
     20-2048 Hz, stopband floor eps = 1e-3, remodulated (undemodulated) tiles of
-    M = 4320 >= N/2 + 1 columns; forward of every tile, then the single-tile
-    inverse from one mid-band tile per segment (spectral division)."""
+    M = 4320 >= N/2 + 1 columns (the compile-time variants built for the dense
+    mode, tuned); forward of every tile, the single-tile inverse from one
+    mid-band tile per segment (spectral division), and the canonical dual
+    inverse of all tiles."""
     import torch
     from oracle import qtam_oracle as O
     from paper_2603_29785_gb300 import qtam, synth
     torch.cuda.set_device(local)
+    from paper_2603_29785_gb300 import tune as qtune
     fs, N, qs, K, eps = 4096.0, 8192, (4.0, 8.0, 16.0), 64, 1e-3
     B = args.batch * 4
     p = qtam.Plan(fs, N, qs, 20.0, 2048.0, K, stopband_eps=eps, remodulate=True, device=local)
+    tuned = qtune.tune(p, B)      # the compile-time variants built for the dense mode (M = 4320)
     xh_ = np.stack([synth.glitchy_segment(500 + b, N, fs, chirp=(b % 2 == 0)) for b in range(B)]).astype(np.float32)
     x = torch.from_numpy(xh_).cuda()
     y = p.forward(x)
@@ -566,21 +570,25 @@ def run_dense(args, local):
     for _ in range(max(3, args.warmup)):
         qtam.qtam_forward(p.handle, x, B, y, ws, wsb, st)
         qtam.qtam_inverse_single_tile(p.handle, y, B, 1, K // 2, xs, ws, wsb, st)
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    xd = torch.empty_like(x)
 
     def timed():
-        tf = ti = 0.0
+        tf = ti = td = 0.0
         for _ in range(args.steps):
             ev[0].record(st)
             qtam.qtam_forward(p.handle, x, B, y, ws, wsb, st)
             ev[1].record(st)
             qtam.qtam_inverse_single_tile(p.handle, y, B, 1, K // 2, xs, ws, wsb, st)
             ev[2].record(st)
-            ev[2].synchronize()
+            qtam.qtam_inverse(p.handle, y, B, 0, xd, ws, wsb, st)
+            ev[3].record(st)
+            ev[3].synchronize()
             tf += ev[0].elapsed_time(ev[1])
             ti += ev[1].elapsed_time(ev[2])
-        return tf / args.steps, ti / args.steps
-    (ms_f, ms_i), clk = _clock_wrap(timed, local)
+            td += ev[2].elapsed_time(ev[3])
+        return tf / args.steps, ti / args.steps, td / args.steps
+    (ms_f, ms_i, ms_d), clk = _clock_wrap(timed, local)
     env_bytes = B * p.info["envelope_bytes_per_segment"]
     line = {"metric": "QTAM dense mode: tiles Msamples/s and single-tile inverse Msamples/s",
             "value": round(B * N / ms_f / 1e3, 2), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -592,6 +600,8 @@ def run_dense(args, local):
             "forward_GB_s": round(env_bytes / (ms_f * 1e-3) / 1e9, 1),
             "single_tile_inverse": {"value": round(B * N / ms_i / 1e3, 2), "ms_per_step": round(ms_i, 4),
                                     "tile": [1, K // 2], "rel_err_vs_input": es},
+            "canonical_inverse": {"value": round(B * N / ms_d / 1e3, 2), "ms_per_step": round(ms_d, 4)},
+            "row_variant": tuned["name"],
             "forward_rel_err_vs_oracle": ef, "clocks": clk}
     print(json.dumps(line), flush=True)
 

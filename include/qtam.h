@@ -123,15 +123,17 @@ typedef struct {
    * envelope pointer is 16-byte aligned, else the CUDA-core rows.  Both
    * directions carry BF16 operand rounding (relative error ~3e-3). */
   int32_t short_dft;
-  /* dense mode (NEXT to the demodulated default; Sec. III alternative
-   * inversion): stopband_eps > 0 gives every window the floor eps wherever it
+  /* dense mode (the alternative inversion of Sec. III, beside the
+   * demodulated default): stopband_eps > 0 gives every window the floor eps wherever it
    * vanishes (outside the support and at its edge points), so each tile
    * spans all N/2+1 bins; n_out (M) must then be >= N/2+1 (default: the
    * smallest 2^a 3^b 5^c above it) and any single tile inverts by spectral
    * division (qtam_inverse_single_tile).  remodulate = 1 multiplies the
    * envelopes by exp(+2 pi i k_c n / M): the undemodulated tile, i.e. the
-   * inverse DFT of the unshifted filtered spectrum X W_k.  Both run the
-   * CUDA-core runtime engine (no compile-time variants, no tensor cores);
+   * inverse DFT of the unshifted filtered spectrum X W_k.  Both run on the
+   * CUDA cores: the compile-time row variants built for the dense mode
+   * where the length has them (FP32 compute and envelopes; M = 4320), else
+   * the runtime engine, which also serves the single-tile inverse;
    * remodulate combined with short_dft = TENSOR, or eps with it, is
    * QTAM_ERR_UNSUPPORTED_SIZE. */
   double stopband_eps;

@@ -22,82 +22,6 @@
 namespace qtam {
 namespace {
 
-// ---- registry of compile-time variants (FP32 compute) ------------------------
-template <class Eng, int E>
-cudaError_t fwd_launch(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
-                       const float2* twM, cudaStream_t st) {
-  const int64_t units = B * n_rows;
-  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
-  const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_forward_s<Eng, E>, smem);
-  k_rows_forward_s<Eng, E><<<(unsigned)blocks, Eng::NT, smem, st>>>(
-      rows, n_rows, Nr, X, static_cast<typename Env<float2, E>::S*>(y), units, twM);
-  return cudaGetLastError();
-}
-template <class Eng, int E>
-cudaError_t inv_launch(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
-                       const void* y, float2* A, int64_t B, const float2* twM, cudaStream_t st) {
-  const int64_t units = B * n_sel;
-  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
-  const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_inverse_s<Eng, E>, smem);
-  k_rows_inverse_s<Eng, E><<<(unsigned)blocks, Eng::NT, smem, st>>>(
-      rows, row_list, n_sel, n_rows, Nr, static_cast<const typename Env<float2, E>::S*>(y), A, units, twM);
-  return cudaGetLastError();
-}
-
-template <class Eng>
-cudaError_t fwd_launch_tab(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
-                           const float2* twM, cudaStream_t st, const float* wtab) {
-  const int64_t units = B * n_rows;
-  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
-  const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_forward_st<Eng, ENV_F32>, smem);
-  k_rows_forward_st<Eng, ENV_F32><<<(unsigned)blocks, Eng::NT, smem, st>>>(rows, n_rows, Nr, X,
-                                                                            static_cast<float2*>(y), units, twM, wtab);
-  return cudaGetLastError();
-}
-template <class Eng>
-cudaError_t inv_launch_tab(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
-                           const void* y, float2* A, int64_t B, const float2* twM, cudaStream_t st,
-                           const float* wtab) {
-  const int64_t units = B * n_sel;
-  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
-  const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_inverse_st<Eng, ENV_F32>, smem);
-  k_rows_inverse_st<Eng, ENV_F32><<<(unsigned)blocks, Eng::NT, smem, st>>>(
-      rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, twM, wtab);
-  return cudaGetLastError();
-}
-
-template <class Eng> RowVariant make_variant(const char* name) {
-  RowVariant v;
-  v.M = Eng::M;
-  v.rows_per_block = 1 << Eng::NBS;
-  v.threads = Eng::NT;
-  v.smem = Eng::smem_bytes(sizeof(float2));
-  v.name = name;
-  v.nst = Eng::nrad;
-  for (int i = 0; i < Eng::nrad; ++i) v.r[i] = Eng::radices[i];
-  v.fwd[ENV_F32] = fwd_launch<Eng, ENV_F32>;
-  v.fwd[ENV_F64] = nullptr;
-  v.fwd[ENV_BF16] = fwd_launch<Eng, ENV_BF16>;
-  v.fwd[ENV_F16] = fwd_launch<Eng, ENV_F16>;
-  v.inv[ENV_F32] = inv_launch<Eng, ENV_F32>;
-  v.inv[ENV_F64] = nullptr;
-  v.inv[ENV_BF16] = inv_launch<Eng, ENV_BF16>;
-  v.inv[ENV_F16] = inv_launch<Eng, ENV_F16>;
-  v.fwd_tab = nullptr;
-  v.inv_tab = nullptr;
-  return v;
-}
-template <class Eng> RowVariant make_variant_tab(const char* name) {
-  RowVariant v = make_variant<Eng>(name);
-  v.fwd_tab = fwd_launch_tab<Eng>;
-  v.inv_tab = inv_launch_tab<Eng>;
-  return v;
-}
-
 // StaticEngine<M, log2 rows per block, min blocks per SM, radices...>; the
 // first variant listed for a length is the default before tuning.
 // QTAM_VT: also built for window tables (the first such variant of a length
@@ -248,8 +172,13 @@ cudaError_t launch_scale_rows(void* y, int env, const float* gain, int64_t n_row
   return cudaGetLastError();
 }
 
-int row_variant_count() { return (int)(sizeof(kVariants) / sizeof(kVariants[0])); }
-const RowVariant* row_variant(int i) { return (i >= 0 && i < row_variant_count()) ? &kVariants[i] : nullptr; }
+// the dense-mode variants follow the ones registered here
+constexpr int kMainVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
+int row_variant_count() { return kMainVariants + dense_row_variant_count(); }
+const RowVariant* row_variant(int i) {
+  if (i < 0) return nullptr;
+  return i < kMainVariants ? &kVariants[i] : dense_row_variant(i - kMainVariants);
+}
 
 template <typename T>
 cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_rows, int64_t Nr, const cplx<T>* X,
@@ -259,10 +188,14 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
   DenseArgs<T> da;
   da.remod = c.remod;
   if constexpr (sizeof(T) == 4) {
-    if (const RowVariant* v = c.remod ? nullptr : row_variant(c.variant)) {
-      if (!wtab) return v->fwd[env](rows, n_rows, Nr, X, y, B, static_cast<const float2*>(c.stw), st);
-      if (env == ENV_F32 && v->fwd_tab)
-        return v->fwd_tab(rows, n_rows, Nr, X, y, B, static_cast<const float2*>(c.stw), st, wtab);
+    if (const RowVariant* v = row_variant(c.variant)) {
+      const float2* stw = static_cast<const float2*>(c.stw);
+      if (c.dense) {
+        if (env == ENV_F32 && v->fwd_dense) return v->fwd_dense(rows, n_rows, Nr, X, y, B, stw, st, wtab, twM, c.remod);
+      } else {
+        if (!wtab) return v->fwd[env](rows, n_rows, Nr, X, y, B, stw, st);
+        if (env == ENV_F32 && v->fwd_tab) return v->fwd_tab(rows, n_rows, Nr, X, y, B, stw, st, wtab);
+      }
     }
   }
   GenericEngine eng{c.rp};
@@ -300,10 +233,15 @@ cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const in
   da.remod = c.remod;
   if (units == 0) return cudaSuccess;
   if constexpr (sizeof(T) == 4) {
-    if (const RowVariant* v = (c.remod || da.divide) ? nullptr : row_variant(c.variant)) {
-      if (!wtab) return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, static_cast<const float2*>(c.stw), st);
-      if (env == ENV_F32 && v->inv_tab)
-        return v->inv_tab(rows, row_list, n_sel, n_rows, Nr, y, A, B, static_cast<const float2*>(c.stw), st, wtab);
+    if (const RowVariant* v = da.divide ? nullptr : row_variant(c.variant)) {
+      const float2* stw = static_cast<const float2*>(c.stw);
+      if (c.dense) {
+        if (env == ENV_F32 && v->inv_dense)
+          return v->inv_dense(rows, row_list, n_sel, n_rows, Nr, y, A, B, stw, st, wtab, twM, c.remod);
+      } else {
+        if (!wtab) return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, stw, st);
+        if (env == ENV_F32 && v->inv_tab) return v->inv_tab(rows, row_list, n_sel, n_rows, Nr, y, A, B, stw, st, wtab);
+      }
     }
   }
   GenericEngine eng{c.rp};

@@ -513,12 +513,14 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
   return QTAM_OK;
 }
 
-// A compile-time row variant serves a plan of its length with FP32 compute,
-// outside the dense mode; plans with a non-bisquare window need a variant
-// built for window tables and FP32 envelopes.
+// A compile-time row variant serves a plan of its length with FP32 compute;
+// plans with a non-bisquare window need a variant built for window tables
+// and FP32 envelopes, dense-mode plans (stopband floor or carrier) one built
+// with the dense kernels and FP32 envelopes.
 bool variant_usable(const qtam_plan_s* pl, int id) {
   const RowVariant* v = row_variant(id);
-  if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32 || pl->eps > 0 || pl->remod) return false;
+  if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32) return false;
+  if (pl->eps > 0 || pl->remod) return v->fwd_dense != nullptr && pl->env == QTAM_DTYPE_F32;
   return pl->all_bisquare() || (v->fwd_tab != nullptr && pl->env == QTAM_DTYPE_F32);
 }
 
@@ -864,6 +866,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.variant = -1;
   pl->rc.tensor = pl->short_dft == QTAM_SHORT_DFT_TENSOR && tc_forward_supported(pl->M);
   pl->rc.remod = pl->remod;
+  pl->rc.dense = pl->eps > 0 || pl->remod;
   if (!dbl) {
     for (int v = 0; v < row_variant_count(); ++v)
       if (variant_usable(pl, v)) {

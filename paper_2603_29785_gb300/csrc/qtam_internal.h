@@ -66,7 +66,8 @@ struct RowCfg {
   int threads;
   size_t smem;
   int variant;   // index of a compile-time row-kernel variant, -1 = runtime engine
-  int remod = 0; // dense mode: remodulated envelopes (runtime engine only)
+  int remod = 0; // dense mode: remodulated envelopes
+  int dense = 0; // stopband floor or carrier: only the variants' dense kernels serve the plan
   const void* stw = nullptr;   // stage twiddle tables of that variant
   // tensor-core short DFT (M = 8192): DFT-64 block operand, its conjugate
   // transpose (the inverse rows), DFT-128 cosine and sine operands; used
@@ -101,6 +102,12 @@ using RowFwdTabFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const fl
                                     cudaStream_t, const float*);
 using RowInvTabFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
                                     const float2*, cudaStream_t, const float*);
+// dense mode (FP32 envelopes): the weights with the stopband floor over the
+// whole one-sided spectrum, and the carrier on store / load when remod is set
+using RowFwdDenseFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const float2*, void*, int64_t, const float2*,
+                                      cudaStream_t, const float*, const float2* twM, int remod);
+using RowInvDenseFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
+                                      const float2*, cudaStream_t, const float*, const float2* twM, int remod);
 struct RowVariant {
   int M;
   int rows_per_block;
@@ -113,7 +120,12 @@ struct RowVariant {
   RowInvFn inv[4];
   RowFwdTabFn fwd_tab;   // null unless built for window tables (FP32 envelopes only)
   RowInvTabFn inv_tab;
+  RowFwdDenseFn fwd_dense;   // null unless built for the dense mode (FP32 envelopes only)
+  RowInvDenseFn inv_dense;
 };
+// the dense-mode variants live in their own translation unit (kernels_rows_dense.cu)
+int dense_row_variant_count();
+const RowVariant* dense_row_variant(int i);
 // Fused streaming row kernels (kernels_rows_stream.cu) of a compile-time
 // variant, looked up by the variant's name: forward with the crop-and-phase
 // store into the map, inverse with the history/new-columns chunk load.

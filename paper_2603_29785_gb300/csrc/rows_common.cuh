@@ -400,5 +400,156 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
                                               wtab);
 }
 
+
+// Dense mode on a compile-time FFT (FP32 envelopes): the weights of the
+// integer-product / table path (c eps wherever the window vanishes, the band
+// spanning the one-sided spectrum through hb) and the carrier
+// e^{+2 pi i k_c n / M} on store (its conjugate on load) when remod is set.
+// tws holds the variant's stage twiddles, twM the plan's M-point table.
+template <class Eng>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB)
+    k_rows_forward_sd(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
+                      float2* __restrict__ y, int64_t n_units, const float2* __restrict__ tws,
+                      const float* __restrict__ wtab, const float2* __restrict__ twM, int remod) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  constexpr int M = Eng::M;
+  const int64_t unit = ((int64_t)blockIdx.x << Eng::NBS) + (threadIdx.x & ((1 << Eng::NBS) - 1));
+  const bool valid = unit < n_units;
+  const int64_t seg = valid ? unit / n_rows : 0;
+  const int row = valid ? (int)(unit - seg * n_rows) : 0;
+  const RowCtx<float, false> rc = row_ctx<float, false>(rows, row, M, Nr, valid, false, wtab);
+  LoadBand<float, false> ld{X + seg * Nr, rc};
+  StoreEnvelopeRT<float2, ENV_F32> stv{y + (valid ? unit : 0) * M, valid, remod, rc.kc % M, M, twM};
+  Eng().template run<+1>(sm, tws, ld, stv);
+}
+template <class Eng>
+__global__ void __launch_bounds__(Eng::NT, Eng::MINB)
+    k_rows_inverse_sd(const RowDev<float>* __restrict__ rows, const int* __restrict__ row_list, int n_sel, int n_rows,
+                      int64_t Nr, const float2* __restrict__ y, float2* __restrict__ A, int64_t n_units,
+                      const float2* __restrict__ tws, const float* __restrict__ wtab, const float2* __restrict__ twM,
+                      int remod) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float2* sm = reinterpret_cast<float2*>(smraw);
+  constexpr int M = Eng::M;
+  const int64_t unit = ((int64_t)blockIdx.x << Eng::NBS) + (threadIdx.x & ((1 << Eng::NBS) - 1));
+  const bool valid = unit < n_units;
+  const int64_t seg = valid ? unit / n_sel : 0;
+  const int row = valid ? row_list[unit - seg * n_sel] : 0;
+  const RowCtx<float, false> rc = row_ctx<float, false>(rows, row, M, Nr, valid, true, wtab);
+  LoadEnvelopeRT<float2, ENV_F32> ld{y + (seg * n_rows + row) * M, valid, remod, rc.kc % M, M, twM};
+  AccumulateBand<float, false, Eng::PRED_RED> acc{A + seg * Nr, rc};
+  Eng().template run<-1>(sm, tws, ld, acc);
+}
+
+// ---- registry entries of compile-time variants (FP32 compute) ----------------
+template <class Eng, int E>
+cudaError_t fwd_launch(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
+                       const float2* twM, cudaStream_t st) {
+  const int64_t units = B * n_rows;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_forward_s<Eng, E>, smem);
+  k_rows_forward_s<Eng, E><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, n_rows, Nr, X, static_cast<typename Env<float2, E>::S*>(y), units, twM);
+  return cudaGetLastError();
+}
+template <class Eng, int E>
+cudaError_t inv_launch(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
+                       const void* y, float2* A, int64_t B, const float2* twM, cudaStream_t st) {
+  const int64_t units = B * n_sel;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_inverse_s<Eng, E>, smem);
+  k_rows_inverse_s<Eng, E><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, row_list, n_sel, n_rows, Nr, static_cast<const typename Env<float2, E>::S*>(y), A, units, twM);
+  return cudaGetLastError();
+}
+
+template <class Eng>
+cudaError_t fwd_launch_tab(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
+                           const float2* twM, cudaStream_t st, const float* wtab) {
+  const int64_t units = B * n_rows;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_forward_st<Eng, ENV_F32>, smem);
+  k_rows_forward_st<Eng, ENV_F32><<<(unsigned)blocks, Eng::NT, smem, st>>>(rows, n_rows, Nr, X,
+                                                                            static_cast<float2*>(y), units, twM, wtab);
+  return cudaGetLastError();
+}
+template <class Eng>
+cudaError_t inv_launch_tab(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
+                           const void* y, float2* A, int64_t B, const float2* twM, cudaStream_t st,
+                           const float* wtab) {
+  const int64_t units = B * n_sel;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_inverse_st<Eng, ENV_F32>, smem);
+  k_rows_inverse_st<Eng, ENV_F32><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, twM, wtab);
+  return cudaGetLastError();
+}
+
+template <class Eng>
+cudaError_t fwd_launch_dense(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
+                             const float2* tws, cudaStream_t st, const float* wtab, const float2* twM, int remod) {
+  const int64_t units = B * n_rows;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_forward_sd<Eng>, smem);
+  k_rows_forward_sd<Eng><<<(unsigned)blocks, Eng::NT, smem, st>>>(rows, n_rows, Nr, X, static_cast<float2*>(y), units,
+                                                                   tws, wtab, twM, remod);
+  return cudaGetLastError();
+}
+template <class Eng>
+cudaError_t inv_launch_dense(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
+                             const void* y, float2* A, int64_t B, const float2* tws, cudaStream_t st,
+                             const float* wtab, const float2* twM, int remod) {
+  const int64_t units = B * n_sel;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_inverse_sd<Eng>, smem);
+  k_rows_inverse_sd<Eng><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, tws, wtab, twM, remod);
+  return cudaGetLastError();
+}
+
+template <class Eng> RowVariant make_variant(const char* name) {
+  RowVariant v;
+  v.M = Eng::M;
+  v.rows_per_block = 1 << Eng::NBS;
+  v.threads = Eng::NT;
+  v.smem = Eng::smem_bytes(sizeof(float2));
+  v.name = name;
+  v.nst = Eng::nrad;
+  for (int i = 0; i < Eng::nrad; ++i) v.r[i] = Eng::radices[i];
+  v.fwd[ENV_F32] = fwd_launch<Eng, ENV_F32>;
+  v.fwd[ENV_F64] = nullptr;
+  v.fwd[ENV_BF16] = fwd_launch<Eng, ENV_BF16>;
+  v.fwd[ENV_F16] = fwd_launch<Eng, ENV_F16>;
+  v.inv[ENV_F32] = inv_launch<Eng, ENV_F32>;
+  v.inv[ENV_F64] = nullptr;
+  v.inv[ENV_BF16] = inv_launch<Eng, ENV_BF16>;
+  v.inv[ENV_F16] = inv_launch<Eng, ENV_F16>;
+  v.fwd_tab = nullptr;
+  v.inv_tab = nullptr;
+  v.fwd_dense = nullptr;
+  v.inv_dense = nullptr;
+  return v;
+}
+template <class Eng> RowVariant make_variant_tab(const char* name) {
+  RowVariant v = make_variant<Eng>(name);
+  v.fwd_tab = fwd_launch_tab<Eng>;
+  v.inv_tab = inv_launch_tab<Eng>;
+  return v;
+}
+// the table variant plus the dense-mode kernels
+template <class Eng> RowVariant make_variant_dense(const char* name) {
+  RowVariant v = make_variant_tab<Eng>(name);
+  v.fwd_dense = fwd_launch_dense<Eng>;
+  v.inv_dense = inv_launch_dense<Eng>;
+  return v;
+}
+
 }  // namespace
 }  // namespace qtam

@@ -27,8 +27,10 @@ def default_cache_path() -> str:
 def _key(plan: "qtam.Plan", batch: int) -> str:
     import torch
     name = torch.cuda.get_device_name(plan.device).replace(" ", "_")
-    i = plan.info
-    return f"{name}|N{plan.N}|P{plan.P}|K{plan.K}|M{plan.M}|B{batch}|{plan.compute}/{plan.envelope}"
+    i, d = plan.info, plan._desc
+    # the plan's kind: window (band_bins tells composite banks apart), dense-mode options, short-DFT engine
+    kind = f"w{d.window}:{d.window_param}:{i['band_bins']}|eps{d.stopband_eps}|rm{d.remodulate}|sd{d.short_dft}"
+    return f"{name}|N{plan.N}|P{plan.P}|K{plan.K}|M{plan.M}|B{batch}|{plan.compute}/{plan.envelope}|{kind}"
 
 
 def _load(path):

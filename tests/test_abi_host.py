@@ -181,7 +181,15 @@ def test_dense_mode_options():
     p = qtam.Plan(*base, stopband_eps=1e-6, p_floor_rel=0.0, device=-1)
     assert p.M == 4320 and p.info["max_window"] == 4097            # smallest 2^a 3^b 5^c >= N/2 + 1
     assert p.info["kept_bins"] == 4097 and p.info["band_bins"] == 32 * 4097   # P > 0 on every bin
-    assert qtam.qtam_plan_variants(p.handle) == [-1]
+    vs = qtam.qtam_plan_variants(p.handle)                          # runtime engine + the dense variants
+    assert vs[0] == -1 and len(vs) == 4 and p.info["row_variant"] == vs[1]
+    names = [qtam.qtam_variant_describe(v)["name"] for v in vs[1:]]
+    assert all(n.startswith("4320:") for n in names)
+    assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, n_out=4800, device=-1).handle) == [-1]
+    assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, envelope="bf16", device=-1).handle) == [-1]
+    assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, compute="f64", device=-1).handle) == [-1]
+    r = qtam.Plan(*base, remodulate=True, n_out=4320, device=-1)     # carrier alone: dense kernels too
+    assert len(qtam.qtam_plan_variants(r.handle)) == 4
     assert _err(lambda: qtam.Plan(*base, stopband_eps=1e-6, n_out=4000, device=-1)) == 3    # aliasing
     assert _err(lambda: qtam.Plan(*base, stopband_eps=-1.0, device=-1)) == 1
     assert _err(lambda: qtam.Plan(*base, n_out=8192, stopband_eps=1e-6, short_dft="tensor", device=-1)) == 2

@@ -63,6 +63,31 @@ def test_dense_forward_and_single_tile_fp32(i, remod, window):
         assert _rel(xh[b], O.projection(g, x[b].astype(np.float64), tau=p.info["p_floor_rel"])) < 1e-5
 
 
+@pytest.mark.parametrize("remod,window", [(False, "bisquare"), (True, "hann")])
+def test_dense_compile_time_variants_match_oracle(remod, window):
+    """M = 4320 has compile-time variants with the dense kernels: each of them
+    and the runtime engine against the oracle, forward and accumulated inverse
+    (odd batch)."""
+    c = CFGS[1]
+    p, g = _make(c, "f32", 1e-3, remod, window)
+    ids = qtam.qtam_plan_variants(p.handle)
+    assert p.info["row_variant"] >= 0 and len(ids) == 4
+    B = 3
+    x = np.stack([synth.glitchy_segment(700 + b, c["N"], c["fs"], chirp=True) for b in range(B)]).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    refs = [O.forward(g, xb.astype(np.float64)) for xb in x]
+    projs = [O.projection(g, xb.astype(np.float64), tau=p.info["p_floor_rel"]) for xb in x]
+    for v in ids:
+        qtam.qtam_plan_set_variant(p.handle, v)
+        y = p.forward(xd)
+        Y = y.cpu().numpy().astype(np.complex128)
+        xh = p.inverse(y).cpu().numpy().astype(np.float64)
+        for b in range(B):
+            assert _rel(Y[b], refs[b]) < 1e-6, v
+            assert np.max(np.abs(Y[b] - refs[b])) <= 1e-5 * np.max(np.abs(refs[b])), v
+            assert _rel(xh[b], projs[b]) < 1e-5, v
+
+
 @pytest.mark.parametrize("remod", [False, True])
 def test_dense_single_tile_fp64(remod):
     c = CFGS[1]
