@@ -866,7 +866,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.variant = -1;
   pl->rc.tensor = pl->short_dft == QTAM_SHORT_DFT_TENSOR && tc_forward_supported(pl->M);
   pl->rc.remod = pl->remod;
-  pl->rc.dense = pl->eps > 0 || pl->remod;
+  pl->rc.dense = (pl->eps > 0 && pl->remod) ? 2 : (pl->eps > 0 || pl->remod) ? 1 : 0;
   if (!dbl) {
     for (int v = 0; v < row_variant_count(); ++v)
       if (variant_usable(pl, v)) {

@@ -67,7 +67,8 @@ struct RowCfg {
   size_t smem;
   int variant;   // index of a compile-time row-kernel variant, -1 = runtime engine
   int remod = 0; // dense mode: remodulated envelopes
-  int dense = 0; // stopband floor or carrier: only the variants' dense kernels serve the plan
+  int dense = 0; // stopband floor or carrier: only the variants' dense kernels serve the plan;
+                 // 2: floor and carrier (tiles span the spectrum, bins at their own positions)
   const void* stw = nullptr;   // stage twiddle tables of that variant
   // tensor-core short DFT (M = 8192): DFT-64 block operand, its conjugate
   // transpose (the inverse rows), DFT-128 cosine and sine operands; used
@@ -103,11 +104,12 @@ using RowFwdTabFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const fl
 using RowInvTabFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
                                     const float2*, cudaStream_t, const float*);
 // dense mode (FP32 envelopes): the weights with the stopband floor over the
-// whole one-sided spectrum, and the carrier on store / load when remod is set
+// whole one-sided spectrum; mode 0 baseband tiles, 1 with the carrier on
+// store / load, 2 floor and carrier (bins placed at their own positions)
 using RowFwdDenseFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const float2*, void*, int64_t, const float2*,
-                                      cudaStream_t, const float*, const float2* twM, int remod);
+                                      cudaStream_t, const float*, const float2* twM, int mode);
 using RowInvDenseFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
-                                      const float2*, cudaStream_t, const float*, const float2* twM, int remod);
+                                      const float2*, cudaStream_t, const float*, const float2* twM, int mode);
 struct RowVariant {
   int M;
   int rows_per_block;

@@ -401,12 +401,46 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
 }
 
 
+// Dense tiles with the carrier, where the band spans all N/2 + 1 bins and
+// M > N/2: the remodulated envelope Y e^{+2 pi i k_c n / M} is the inverse
+// DFT of the weighted spectrum placed at its own bins (position i holds bin
+// i, the offset from the centre is i - k_c), so neither the roll to
+// baseband nor a carrier multiply is needed; the inverse reads bin i's
+// analysis value at position i the same way.
+template <typename T> struct LoadSpectrumAbs {
+  using V = cplx<T>;
+  const V* Xs;
+  RowCtx<T, false> r;
+  int nhalf;
+  __device__ __forceinline__ V get(int, int i) const {
+    V x = mk<V>((T)0, (T)0);
+    if (i <= nhalf) x = Xs[i];
+    return cscale(x, r.weight(i - r.kc));
+  }
+};
+template <typename T, bool PRED> struct AccumulateAbs {
+  using V = cplx<T>;
+  V* As;
+  RowCtx<T, false> r;
+  int nhalf;
+  __device__ __forceinline__ void put(int, int i, V v) const {
+    const T w = r.weight(i - r.kc);
+    if constexpr (PRED) {
+      add_if(&As[i], cscale(v, w), i <= nhalf);
+    } else if (i <= nhalf) {
+      add_if(&As[i], cscale(v, w), true);
+    }
+  }
+};
+
 // Dense mode on a compile-time FFT (FP32 envelopes): the weights of the
 // integer-product / table path (c eps wherever the window vanishes, the band
-// spanning the one-sided spectrum through hb) and the carrier
-// e^{+2 pi i k_c n / M} on store (its conjugate on load) when remod is set.
-// tws holds the variant's stage twiddles, twM the plan's M-point table.
-template <class Eng>
+// spanning the one-sided spectrum through hb).  ABS: tiles with the carrier
+// and the floor, bins at their own positions (above); otherwise the band at
+// baseband with the carrier e^{+2 pi i k_c n / M} from the plan's M-point
+// table on store (its conjugate on load) when remod is set.  tws holds the
+// variant's stage twiddles, twM the plan's M-point table.
+template <class Eng, bool ABS>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
     k_rows_forward_sd(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
                       float2* __restrict__ y, int64_t n_units, const float2* __restrict__ tws,
@@ -419,11 +453,17 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
   const int64_t seg = valid ? unit / n_rows : 0;
   const int row = valid ? (int)(unit - seg * n_rows) : 0;
   const RowCtx<float, false> rc = row_ctx<float, false>(rows, row, M, Nr, valid, false, wtab);
-  LoadBand<float, false> ld{X + seg * Nr, rc};
-  StoreEnvelopeRT<float2, ENV_F32> stv{y + (valid ? unit : 0) * M, valid, remod, rc.kc % M, M, twM};
-  Eng().template run<+1>(sm, tws, ld, stv);
+  if constexpr (ABS) {
+    LoadSpectrumAbs<float> ld{X + seg * Nr, rc, valid ? (int)(Nr - 1) : -1};
+    StoreEnvelope<float2, ENV_F32> stv{y + (valid ? unit : 0) * M, valid};
+    Eng().template run<+1>(sm, tws, ld, stv);
+  } else {
+    LoadBand<float, false> ld{X + seg * Nr, rc};
+    StoreEnvelopeRT<float2, ENV_F32> stv{y + (valid ? unit : 0) * M, valid, remod, rc.kc % M, M, twM};
+    Eng().template run<+1>(sm, tws, ld, stv);
+  }
 }
-template <class Eng>
+template <class Eng, bool ABS>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
     k_rows_inverse_sd(const RowDev<float>* __restrict__ rows, const int* __restrict__ row_list, int n_sel, int n_rows,
                       int64_t Nr, const float2* __restrict__ y, float2* __restrict__ A, int64_t n_units,
@@ -437,9 +477,15 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
   const int64_t seg = valid ? unit / n_sel : 0;
   const int row = valid ? row_list[unit - seg * n_sel] : 0;
   const RowCtx<float, false> rc = row_ctx<float, false>(rows, row, M, Nr, valid, true, wtab);
-  LoadEnvelopeRT<float2, ENV_F32> ld{y + (seg * n_rows + row) * M, valid, remod, rc.kc % M, M, twM};
-  AccumulateBand<float, false, Eng::PRED_RED> acc{A + seg * Nr, rc};
-  Eng().template run<-1>(sm, tws, ld, acc);
+  if constexpr (ABS) {
+    LoadEnvelope<float2, ENV_F32> ld{y + (seg * n_rows + row) * M, valid};
+    AccumulateAbs<float, Eng::PRED_RED> acc{A + seg * Nr, rc, valid ? (int)(Nr - 1) : -1};
+    Eng().template run<-1>(sm, tws, ld, acc);
+  } else {
+    LoadEnvelopeRT<float2, ENV_F32> ld{y + (seg * n_rows + row) * M, valid, remod, rc.kc % M, M, twM};
+    AccumulateBand<float, false, Eng::PRED_RED> acc{A + seg * Nr, rc};
+    Eng().template run<-1>(sm, tws, ld, acc);
+  }
 }
 
 // ---- registry entries of compile-time variants (FP32 compute) ----------------
@@ -490,28 +536,44 @@ cudaError_t inv_launch_tab(const RowDev<float>* rows, const int* row_list, int n
   return cudaGetLastError();
 }
 
-template <class Eng>
-cudaError_t fwd_launch_dense(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
-                             const float2* tws, cudaStream_t st, const float* wtab, const float2* twM, int remod) {
+// mode: 0 baseband tiles, 1 baseband tiles with the carrier, 2 tiles spanning
+// the spectrum with the carrier (bins at their own positions)
+template <class Eng, bool ABS>
+cudaError_t fwd_launch_dense_k(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
+                               const float2* tws, cudaStream_t st, const float* wtab, const float2* twM, int remod) {
   const int64_t units = B * n_rows;
   const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
   const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_forward_sd<Eng>, smem);
-  k_rows_forward_sd<Eng><<<(unsigned)blocks, Eng::NT, smem, st>>>(rows, n_rows, Nr, X, static_cast<float2*>(y), units,
-                                                                   tws, wtab, twM, remod);
+  allow_smem((const void*)k_rows_forward_sd<Eng, ABS>, smem);
+  k_rows_forward_sd<Eng, ABS><<<(unsigned)blocks, Eng::NT, smem, st>>>(rows, n_rows, Nr, X, static_cast<float2*>(y),
+                                                                        units, tws, wtab, twM, remod);
+  return cudaGetLastError();
+}
+template <class Eng>
+cudaError_t fwd_launch_dense(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
+                             const float2* tws, cudaStream_t st, const float* wtab, const float2* twM, int mode) {
+  return mode == 2 ? fwd_launch_dense_k<Eng, true>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, 0)
+                   : fwd_launch_dense_k<Eng, false>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, mode);
+}
+template <class Eng, bool ABS>
+cudaError_t inv_launch_dense_k(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
+                               const void* y, float2* A, int64_t B, const float2* tws, cudaStream_t st,
+                               const float* wtab, const float2* twM, int remod) {
+  const int64_t units = B * n_sel;
+  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
+  const size_t smem = Eng::smem_bytes(sizeof(float2));
+  allow_smem((const void*)k_rows_inverse_sd<Eng, ABS>, smem);
+  k_rows_inverse_sd<Eng, ABS><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, tws, wtab, twM, remod);
   return cudaGetLastError();
 }
 template <class Eng>
 cudaError_t inv_launch_dense(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
                              const void* y, float2* A, int64_t B, const float2* tws, cudaStream_t st,
-                             const float* wtab, const float2* twM, int remod) {
-  const int64_t units = B * n_sel;
-  const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
-  const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_inverse_sd<Eng>, smem);
-  k_rows_inverse_sd<Eng><<<(unsigned)blocks, Eng::NT, smem, st>>>(
-      rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, tws, wtab, twM, remod);
-  return cudaGetLastError();
+                             const float* wtab, const float2* twM, int mode) {
+  return mode == 2 ? inv_launch_dense_k<Eng, true>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM, 0)
+                   : inv_launch_dense_k<Eng, false>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM,
+                                                    mode);
 }
 
 template <class Eng> RowVariant make_variant(const char* name) {
