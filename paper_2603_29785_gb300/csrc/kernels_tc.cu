@@ -460,14 +460,38 @@ __device__ __forceinline__ void red_add_if(float2* p, float v0, float v1, bool o
 // 64 n2 .. + 7; the 8 lanes of a quarter warp take 8 consecutive n2 of one
 // octet, so their 16-byte stores fill one core matrix (no bank conflicts)
 // and each lane reads whole 32-byte sectors.
-template <int E>
-__device__ __forceinline__ const typename TcEnv<E>::S* tc_row_ptr(int64_t pr, int r, int64_t n_units, int n_sel,
-                                                                 int n_rows, const int* __restrict__ row_list,
-                                                                 const typename TcEnv<E>::S* __restrict__ y) {
-  const int64_t u = 2 * pr + r;
-  if (u >= n_units) return nullptr;
-  const int64_t seg = u / n_sel;
-  return y + (seg * n_rows + row_list[u - seg * n_sel]) * (int64_t)kTcM;
+// Per-row metadata of a pair (a four-slot ring in shared memory, filled two
+// pairs ahead by threads 0 and 1): the envelope row's offset (-1: no unit)
+// and the band parameters, so that the envelope loads and the accumulation
+// start without dependent reads of the row list and the row table.
+struct TcMeta {
+  long long yoff;   // (seg * n_rows + row) * M, or -1
+  long long aoff;   // seg * Nr + k_c
+  int h, woff, dhi, mlo;
+  float kw, cw;     // kw_inv, c_inv
+};
+
+// the row-list read of unit (pair pk, row r): first step of a metadata fill
+__device__ __forceinline__ bool tc_meta_unit(int64_t pk, int r, int64_t n_pairs, int64_t n_units, int n_sel,
+                                             const int* __restrict__ row_list, int64_t& seg, int& row) {
+  const int64_t u = 2 * pk + r;
+  if (pk >= n_pairs || u >= n_units) return false;
+  seg = u / n_sel;
+  row = row_list[u - seg * n_sel];
+  return true;
+}
+__device__ __forceinline__ TcMeta tc_meta_make(bool valid, int64_t seg, int row, const RowDev<float>& rd, int n_rows,
+                                               int64_t Nr) {
+  TcMeta m;
+  m.yoff = valid ? (seg * n_rows + row) * (int64_t)kTcM : -1;
+  m.aoff = seg * Nr + rd.kc;
+  m.h = rd.h;
+  m.woff = rd.woff;
+  m.dhi = (int)min((int64_t)rd.h, Nr - 1 - rd.kc);
+  m.mlo = kTcM + max(-rd.h, -rd.kc);
+  m.kw = rd.kw_inv;
+  m.cw = rd.c_inv;
+  return m;
 }
 
 template <int E>
@@ -495,30 +519,26 @@ __device__ __forceinline__ void tc_store_row(unsigned char* sY, int r, bool vali
   }
 }
 
-// Band accumulation of pair pr from tensor memory (S of row r in columns
-// 128 r: Re over j1, 128 r + 64: Im).  Warp (q4, quarter) reads lanes j2 =
-// 32 q4 + lane of row r = quarter >> 1, j1 in 32 (quarter & 1) .. + 31;
-// blocks of 16 j1 wholly outside the band are skipped by the whole warp.
-__device__ __forceinline__ void tc_accumulate(uint32_t tbase, int64_t pr, int64_t n_units, int n_sel,
-                                              const int* __restrict__ row_list, const RowDev<float>* __restrict__ rows,
-                                              int64_t Nr, float2* __restrict__ A, const float* __restrict__ wtab) {
+// Band accumulation of a pair from tensor memory (S of row r in columns
+// 128 r: Re over j1, 128 r + 64: Im), its rows described by meta[0..1].
+// Warp (q4, quarter) reads lanes j2 = 32 q4 + lane of row r = quarter >> 1,
+// j1 in 32 (quarter & 1) .. + 31; blocks of 16 j1 wholly outside the band
+// are skipped by the whole warp.
+__device__ __forceinline__ void tc_accumulate(uint32_t tbase, const TcMeta* meta, float2* __restrict__ A,
+                                              const float* __restrict__ wtab) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q4 = warp & 3, quarter = warp >> 2;
   const int r = quarter >> 1, jb = 32 * (quarter & 1), j2 = 32 * q4 + lane;
-  const int64_t u = 2 * pr + r;
-  if (u >= n_units) return;   // r is uniform per warp
-  const int64_t seg = u / n_sel;
-  const RowDev<float> rd = rows[row_list[u - seg * n_sel]];
-  const int dhi = (int)min((int64_t)rd.h, Nr - 1 - rd.kc);
-  const int mlo = kTcM + max(-rd.h, -rd.kc);
-  float2* As = A + seg * Nr + rd.kc;
-  const bool tab = wtab != nullptr && rd.woff >= 0;
-  const float h2 = (float)rd.h * (float)rd.h;   // exact: h < 4096
+  const TcMeta m = meta[r];
+  if (m.yoff < 0) return;   // r is uniform per warp
+  float2* As = A + m.aoff;
+  const bool tab = wtab != nullptr && m.woff >= 0;
+  const float h2 = (float)m.h * (float)m.h;   // exact: h < 4096
   const uint32_t lrow = (uint32_t)(32 * q4) << 16;
 #pragma unroll 1
   for (int q = 0; q < 2; ++q) {
     const int j10 = jb + 16 * q;
-    if (!(128 * j10 + 32 * q4 <= dhi || 128 * (j10 + 15) + 32 * q4 + 31 >= mlo)) continue;
+    if (!(128 * j10 + 32 * q4 <= m.dhi || 128 * (j10 + 15) + 32 * q4 + 31 >= m.mlo)) continue;
     float vr[16], vi[16];
     tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(128 * r + j10), vr);
     tc::tmem_ld16_nowait(tbase + lrow + (uint32_t)(128 * r + 64 + j10), vi);
@@ -526,14 +546,14 @@ __device__ __forceinline__ void tc_accumulate(uint32_t tbase, int64_t pr, int64_
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int j = 128 * (j10 + e) + j2;
-      const bool lo = j <= dhi, hi = j >= mlo;
+      const bool lo = j <= m.dhi, hi = j >= m.mlo;
       const int d = lo ? j : j - kTcM;
       float w;
       if (tab) {
-        w = rd.c_inv * wtab[rd.woff + min(d < 0 ? -d : d, rd.h)];
+        w = m.cw * wtab[m.woff + min(d < 0 ? -d : d, m.h)];
       } else {
         const float df = (float)d;
-        const float t = (h2 - df * df) * rd.kw_inv;
+        const float t = (h2 - df * df) * m.kw;
         w = t * t;
       }
       red_add_if(As + d, vr[e] * w, vi[e] * w, lo || hi);
@@ -550,6 +570,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t mbarA, mbarB;
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
+  __shared__ TcMeta smeta[4][2];      // pair of iteration i in slot i & 3
   unsigned char* sAi = sm;            // conjugate DFT-64 block, [128 n][128 k] K-major (GEMM A''s B)
   unsigned char* sGr = sm + 32768;    // [128 j2][128 n2]
   unsigned char* sGi = sm + 65536;
@@ -575,11 +596,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr float kAng = 6.28318530717958647692f / (float)kTcM;
   const int64_t n_pairs = (n_units + 1) >> 1;
   int64_t pr = blockIdx.x;
+  // metadata of the first two pairs (iterations 0 and 1)
+  if (tid < 4) {
+    const int it = tid >> 1, r = tid & 1;
+    int64_t seg = 0;
+    int row = 0;
+    const bool ok = tc_meta_unit(pr + it * (int64_t)gridDim.x, r, n_pairs, n_units, n_sel, row_list, seg, row);
+    smeta[it][r] = tc_meta_make(ok, seg, row, rows[ok ? row : 0], n_rows, Nr);
+  }
+  __syncthreads();
   typename TcLoad<E>::Raw raw[2];
   if (pr < n_pairs) {
 #pragma unroll 1
     for (int r = 0; r < 2; ++r) {
-      const typename TcEnv<E>::S* yr = tc_row_ptr<E>(pr, r, n_units, n_sel, n_rows, row_list, y);
+      const long long yo = smeta[0][r].yoff;
+      const typename TcEnv<E>::S* yr = yo >= 0 ? y + yo : nullptr;
       tc_load_row<E>(yr, raw);
       tc_store_row<E>(sY, r, yr != nullptr, raw);
     }
@@ -593,9 +624,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const uint32_t aY = tc::smem_addr(sY), aE = tc::smem_addr(sE);
   uint32_t phA = 0, phB = 0;
   bool pendA = false, pendB = false;
-  int64_t prev = -1;
+  int prev_slot = -1;
 
-  for (; pr < n_pairs; pr += gridDim.x) {
+  for (int it = 0; pr < n_pairs; pr += gridDim.x, ++it) {
     // ---- GEMM B': Re E [tmem 256..383], Im E [384..511] ----
     if (tid == 0) {
       const uint32_t id = tc::make_idesc_bf16(128, 128, false, false, true),
@@ -622,13 +653,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     // below, stored once GEMM B' has released sY; row 1 under the twiddle,
     // stored under GEMM A'.
     const int64_t nx = pr + gridDim.x;
-    const typename TcEnv<E>::S* ynx0 =
-        nx < n_pairs ? tc_row_ptr<E>(nx, 0, n_units, n_sel, n_rows, row_list, y) : nullptr;
-    const typename TcEnv<E>::S* ynx1 =
-        nx < n_pairs ? tc_row_ptr<E>(nx, 1, n_units, n_sel, n_rows, row_list, y) : nullptr;
+    const long long yo0 = smeta[(it + 1) & 3][0].yoff, yo1 = smeta[(it + 1) & 3][1].yoff;
+    const typename TcEnv<E>::S* ynx0 = nx < n_pairs && yo0 >= 0 ? y + yo0 : nullptr;
+    const typename TcEnv<E>::S* ynx1 = nx < n_pairs && yo1 >= 0 ? y + yo1 : nullptr;
+    // metadata of the pair two iterations ahead: the row-list read now, the
+    // row-table read after GEMM B', the slot written after the twiddle
+    int64_t mseg = 0;
+    int mrow = 0;
+    bool mok = false;
+    if (tid < 2) mok = tc_meta_unit(pr + 2 * (int64_t)gridDim.x, tid, n_pairs, n_units, n_sel, row_list, mseg, mrow);
     tc_load_row<E>(ynx0, raw);
     // ... overlapped with the previous pair's band accumulation (S columns are not touched by GEMM B')
-    if (prev >= 0) tc_accumulate(tbase, prev, n_units, n_sel, row_list, rows, Nr, A, wtab);
+    if (prev_slot >= 0) tc_accumulate(tbase, smeta[prev_slot], A, wtab);
     if (!tc::mbar_wait_bounded(&mbarB, phB, tc::kWaitCycles)) abort_flag = 1;
     tc::fence_after_sync();
     tc::fence_before_sync();
@@ -637,6 +673,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (abort_flag) break;
     phB ^= 1u;
     pendB = false;
+    RowDev<float> mrd;
+    if (tid < 2) mrd = rows[mok ? mrow : 0];
     if (nx < n_pairs) tc_store_row<E>(sY, 0, ynx0 != nullptr, raw);
     tc_load_row<E>(ynx1, raw);
     // ---- twiddle: E -> E'^T (row rr at 32 KB rr, [128 j2][128 k = Re n1 | Im n1], M-major) ----
@@ -670,6 +708,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
     }
+    if (tid < 2) smeta[(it + 2) & 3][tid] = tc_meta_make(mok, mseg, mrow, mrd, n_rows, Nr);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -696,9 +735,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (abort_flag) break;
     phA ^= 1u;
     pendA = false;
-    prev = pr;
+    prev_slot = it & 3;
   }
-  if (!abort_flag && prev >= 0) tc_accumulate(tbase, prev, n_units, n_sel, row_list, rows, Nr, A, wtab);
+  if (!abort_flag && prev_slot >= 0) tc_accumulate(tbase, smeta[prev_slot], A, wtab);
   if (abort_flag) {
     if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
     if (pendA) tc::mbar_wait_bounded(&mbarA, phA, tc::kWaitCycles);

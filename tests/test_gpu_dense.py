@@ -27,11 +27,11 @@ CFGS = [
 ]
 
 
-def _make(c, compute, eps, remod, window="bisquare"):
+def _make(c, compute, eps, remod, window="bisquare", n_out=0):
     p = qtam.Plan(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], compute=compute, stopband_eps=eps,
-                  remodulate=remod, window=window, device=0)
+                  remodulate=remod, window=window, n_out=n_out, device=0)
     g = O.geometry(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], stopband_eps=eps, remodulate=remod,
-                   window=window)
+                   window=window, n_out=n_out)
     assert p.M == g.M and p.M >= g.Nr
     return p, g
 
@@ -63,13 +63,15 @@ def test_dense_forward_and_single_tile_fp32(i, remod, window):
         assert _rel(xh[b], O.projection(g, x[b].astype(np.float64), tau=p.info["p_floor_rel"])) < 1e-5
 
 
-@pytest.mark.parametrize("remod,window", [(False, "bisquare"), (True, "hann")])
-def test_dense_compile_time_variants_match_oracle(remod, window):
+@pytest.mark.parametrize("eps,remod,window", [(1e-3, False, "bisquare"), (1e-3, True, "hann"),
+                                              (0.0, True, "bisquare")])
+def test_dense_compile_time_variants_match_oracle(eps, remod, window):
     """M = 4320 has compile-time variants with the dense kernels: each of them
     and the runtime engine against the oracle, forward and accumulated inverse
-    (odd batch)."""
+    (odd batch).  Floor alone: baseband tiles; floor and carrier: bins at
+    their own positions; carrier alone: baseband tiles times the carrier."""
     c = CFGS[1]
-    p, g = _make(c, "f32", 1e-3, remod, window)
+    p, g = _make(c, "f32", eps, remod, window, n_out=4320)
     ids = qtam.qtam_plan_variants(p.handle)
     assert p.info["row_variant"] >= 0 and len(ids) == 4
     B = 3
