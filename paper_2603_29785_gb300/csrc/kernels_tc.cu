@@ -196,10 +196,13 @@ __device__ __forceinline__ void tc_fill_z(unsigned char* sZ, int64_t pr, int64_t
 
 // Envelopes of pair pr from tensor memory (Re Y in columns 256.., Im Y in
 // 384..) to y[u][n1 + 64 n2]; lanes are rows 64 r + n1, so a warp's stores
-// are 32 consecutive envelope samples.
+// are 32 consecutive envelope samples.  Each warp owns 32 values of n2 and
+// stores them in two halves (q = q0 .. q1 - 1 of 2), so the kernel can issue
+// one half under GEMM A and the other after the twiddle instead of one
+// burst of stores from every SM at once.
 template <int E>
 __device__ __forceinline__ void tc_store_y(uint32_t tbase, int64_t pr, int64_t n_units,
-                                           typename TcEnv<E>::S* __restrict__ y) {
+                                           typename TcEnv<E>::S* __restrict__ y, int q0, int q1) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int q4 = warp & 3, quarter = warp >> 2;   // lane quarter, quarter of the n2 range
   const int r = q4 >> 1, n1 = 32 * (q4 & 1) + lane;
@@ -208,7 +211,7 @@ __device__ __forceinline__ void tc_store_y(uint32_t tbase, int64_t pr, int64_t n
   typename TcEnv<E>::S* yu = y + u * kTcM + n1;
   const uint32_t lrow = (uint32_t)(32 * q4) << 16;
 #pragma unroll 1
-  for (int q = 0; q < 2; ++q) {
+  for (int q = q0; q < q1; ++q) {
     const int n20 = 32 * quarter + 16 * q;
     float vr[16], vi[16];
     tc::tmem_ld16_nowait(tbase + lrow + 256u + (uint32_t)n20, vr);
@@ -279,8 +282,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       tc::mma_commit(&mbarA);
     }
     pendA = true;
-    // ... overlapped with the previous pair's envelope stores (Y columns are not touched by GEMM A)
-    if (prev >= 0) tc_store_y<E>(tbase, prev, n_units, y);
+    // ... overlapped with the first half of the previous pair's envelope stores (Y columns are not
+    // touched by GEMM A)
+    if (prev >= 0) tc_store_y<E>(tbase, prev, n_units, y, 0, 1);
     if (!tc::mbar_wait_bounded(&mbarA, phA, tc::kWaitCycles)) abort_flag = 1;
     tc::fence_after_sync();
     __syncthreads();
@@ -317,6 +321,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
     }
+    // the second half of the previous pair's stores, before GEMM B overwrites the Y columns
+    if (prev >= 0) tc_store_y<E>(tbase, prev, n_units, y, 1, 2);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -354,7 +360,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     pendB = false;
     prev = pr;
   }
-  if (!abort_flag && prev >= 0) tc_store_y<E>(tbase, prev, n_units, y);
+  if (!abort_flag && prev >= 0) tc_store_y<E>(tbase, prev, n_units, y, 0, 2);
   if (abort_flag) {
     if (tid == 0) atomicAdd(&g_tc_timeouts, 1);
     if (pendA) tc::mbar_wait_bounded(&mbarA, phA, tc::kWaitCycles);
