@@ -754,7 +754,7 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   if (!std::isfinite(d->stopband_eps) || d->stopband_eps < 0 || (d->remodulate != 0 && d->remodulate != 1))
     return fail(QTAM_ERR_INVALID_ARG, "stopband_eps must be finite and >= 0, remodulate 0 or 1");
   if ((d->stopband_eps > 0 || d->remodulate) && d->short_dft == QTAM_SHORT_DFT_TENSOR)
-    return fail(QTAM_ERR_UNSUPPORTED_SIZE, "the dense mode runs on the CUDA-core runtime engine");
+    return fail(QTAM_ERR_UNSUPPORTED_SIZE, "the dense mode runs on the CUDA cores, not the tensor-core short DFT");
   if (d->short_dft == QTAM_SHORT_DFT_TENSOR && (d->compute_dtype != QTAM_DTYPE_F32 || d->n_out != 8192))
     return fail(QTAM_ERR_UNSUPPORTED_SIZE, "the tensor-core short DFT needs n_out = 8192 and F32 compute");
 
