@@ -166,3 +166,25 @@ def test_stream_fused_row_kernels_m600():
     assert _rel(xh, O.stream_inverse(g, Yg, hop, tau=tau)) < 1e-5
     xm = _np(s2.inverse(Y, plane_mask=0b010))
     assert _rel(xm, O.stream_inverse(g, Yg, hop, planes=[1], tau=tau)) < 1e-5
+
+
+def test_stream_over_tensor_core_plan():
+    """A stream over a plan with the tensor-core short DFT (M = 8192, both
+    directions on tcgen05) against the oracle's stream, at the BF16 bound of
+    the tensor-core rows (relative 1e-2)."""
+    cfg = dict(fs=4096.0, N=32768, qs=(8.0, 16.0), fmin=20.0, fmax=2048.0, K=32, n_out=8192)
+    t0 = qtam.qtam_tc_status()
+    p, g = _plan(cfg, short_dft="tensor")
+    hop = 16384
+    s = qtam.Stream(p, hop=hop, max_chunks=4)
+    J = 6
+    x = synth.glitchy_segment(17, J * hop, 4096.0, chirp=True).astype(np.float32)
+    Y = _push(s, torch.from_numpy(x).cuda(), [2, 1, 3])
+    Yo = O.stream_forward(g, x.astype(np.float64), hop)
+    Yg = _np(Y)
+    assert Yg.shape == Yo.shape
+    assert _rel(Yg, Yo) < 1e-2
+    xh = _np(s.inverse(Y.contiguous()))
+    xo = O.stream_inverse(g, Yg, hop, tau=p.info["p_floor_rel"])
+    assert _rel(xh, xo) < 2e-2
+    assert qtam.qtam_tc_status() == t0
