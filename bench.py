@@ -329,6 +329,27 @@ def run_gpu(args, rank, world, local):
     e2e = {"value": samples_per_step / e2e_s / 1e6, "unit": UNIT, "h2d_bytes_per_step": B * N * 4,
            "d2h_bytes_per_step": B * N * 4, "ms_per_step": e2e_s * 1e3}
 
+    # ---- the plain per-segment path on the same GPU and plan: one qtam_forward +
+    # qtam_inverse call pair per segment (the same kernels at batch 1: the same numbers) ----
+    def per_segment():
+        for b in range(B):
+            qtam.qtam_forward(h, x[b:b + 1], 1, y[b:b + 1], ws, wsb, st)
+            qtam.qtam_inverse(h, y[b:b + 1], 1, 0, xh[b:b + 1], ws, wsb, st)
+
+    for _ in range(2):
+        per_segment()
+    ps_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        ev[0].record(st)
+        per_segment()
+        ev[4].record(st)
+        ev[4].synchronize()
+        ps_ms += ev[0].elapsed_time(ev[4])
+    ps_ms = reduce_max(ps_ms / args.steps, dist, dev)
+    per_seg = {"value": round(samples_per_step / (ps_ms * 1e-3) / 1e6, 2), "unit": UNIT, "ms_per_step": round(ps_ms, 4),
+               "path": "the same segments, one qtam_forward + qtam_inverse call pair per segment"}
+
     # ---- roofline of the dominant kernel (envelope kernel: writes B*P*K*M complex64) ----
     peaks = {}
     try:
@@ -367,6 +388,7 @@ def run_gpu(args, rank, world, local):
         "path_hbm_frac": round(path_frac, 4),
         "stages": kernels,
         "e2e": e2e,
+        "per_segment_path": per_seg,
         # per step: k_col_forward, k_row_forward, k_untangle_forward (spectrum), k_rows_forward_s
         # (envelopes), k_rows_inverse_s (accumulate; the zeroing is a memset, not a kernel),
         # k_untangle_inverse, k_row_inverse, k_col_inverse (synthesis) -- as the ncu launch list shows

@@ -132,7 +132,8 @@ typedef struct {
    * envelopes by exp(+2 pi i k_c n / M): the undemodulated tile, i.e. the
    * inverse DFT of the unshifted filtered spectrum X W_k.  Both run on the
    * CUDA cores: the compile-time row variants built for the dense mode
-   * where the length has them (FP32 compute and envelopes; M = 4320), else
+   * where the length has them (FP32 compute, any envelope storage;
+   * M = 4320), else
    * the runtime engine, which also serves the single-tile inverse;
    * remodulate combined with short_dft = TENSOR, or eps with it, is
    * QTAM_ERR_UNSUPPORTED_SIZE. */

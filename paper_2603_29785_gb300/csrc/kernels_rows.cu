@@ -191,8 +191,8 @@ cudaError_t launch_rows_forward(const RowCfg& c, const RowDev<T>* rows, int n_ro
     if (const RowVariant* v = row_variant(c.variant)) {
       const float2* stw = static_cast<const float2*>(c.stw);
       if (c.dense) {
-        if (env == ENV_F32 && v->fwd_dense)
-          return v->fwd_dense(rows, n_rows, Nr, X, y, B, stw, st, wtab, twM, c.dense == 2 ? 2 : c.remod);
+        if (v->fwd_dense)
+          return v->fwd_dense(rows, n_rows, Nr, X, y, B, stw, st, wtab, twM, c.dense == 2 ? 2 : c.remod, env);
       } else {
         if (!wtab) return v->fwd[env](rows, n_rows, Nr, X, y, B, stw, st);
         if (env == ENV_F32 && v->fwd_tab) return v->fwd_tab(rows, n_rows, Nr, X, y, B, stw, st, wtab);
@@ -237,8 +237,9 @@ cudaError_t launch_rows_inverse(const RowCfg& c, const RowDev<T>* rows, const in
     if (const RowVariant* v = da.divide ? nullptr : row_variant(c.variant)) {
       const float2* stw = static_cast<const float2*>(c.stw);
       if (c.dense) {
-        if (env == ENV_F32 && v->inv_dense)
-          return v->inv_dense(rows, row_list, n_sel, n_rows, Nr, y, A, B, stw, st, wtab, twM, c.dense == 2 ? 2 : c.remod);
+        if (v->inv_dense)
+          return v->inv_dense(rows, row_list, n_sel, n_rows, Nr, y, A, B, stw, st, wtab, twM, c.dense == 2 ? 2 : c.remod,
+                              env);
       } else {
         if (!wtab) return v->inv[env](rows, row_list, n_sel, n_rows, Nr, y, A, B, stw, st);
         if (env == ENV_F32 && v->inv_tab) return v->inv_tab(rows, row_list, n_sel, n_rows, Nr, y, A, B, stw, st, wtab);

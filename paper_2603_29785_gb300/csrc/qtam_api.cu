@@ -516,11 +516,11 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
 // A compile-time row variant serves a plan of its length with FP32 compute;
 // plans with a non-bisquare window need a variant built for window tables
 // and FP32 envelopes, dense-mode plans (stopband floor or carrier) one built
-// with the dense kernels and FP32 envelopes.
+// with the dense kernels (any envelope storage).
 bool variant_usable(const qtam_plan_s* pl, int id) {
   const RowVariant* v = row_variant(id);
   if (!v || v->M != pl->M || pl->compute != QTAM_DTYPE_F32) return false;
-  if (pl->eps > 0 || pl->remod) return v->fwd_dense != nullptr && pl->env == QTAM_DTYPE_F32;
+  if (pl->eps > 0 || pl->remod) return v->fwd_dense != nullptr;   // F32, BF16 or F16 envelopes
   return pl->all_bisquare() || (v->fwd_tab != nullptr && pl->env == QTAM_DTYPE_F32);
 }
 

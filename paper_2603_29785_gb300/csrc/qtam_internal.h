@@ -103,13 +103,14 @@ using RowFwdTabFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const fl
                                     cudaStream_t, const float*);
 using RowInvTabFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
                                     const float2*, cudaStream_t, const float*);
-// dense mode (FP32 envelopes): the weights with the stopband floor over the
-// whole one-sided spectrum; mode 0 baseband tiles, 1 with the carrier on
-// store / load, 2 floor and carrier (bins placed at their own positions)
+// dense mode (FP32 arithmetic; envelopes F32, BF16 or F16 by EnvKind env):
+// the weights with the stopband floor over the whole one-sided spectrum;
+// mode 0 baseband tiles, 1 with the carrier on store / load, 2 floor and
+// carrier (bins placed at their own positions)
 using RowFwdDenseFn = cudaError_t (*)(const RowDev<float>*, int, int64_t, const float2*, void*, int64_t, const float2*,
-                                      cudaStream_t, const float*, const float2* twM, int mode);
+                                      cudaStream_t, const float*, const float2* twM, int mode, int env);
 using RowInvDenseFn = cudaError_t (*)(const RowDev<float>*, const int*, int, int, int64_t, const void*, float2*, int64_t,
-                                      const float2*, cudaStream_t, const float*, const float2* twM, int mode);
+                                      const float2*, cudaStream_t, const float*, const float2* twM, int mode, int env);
 struct RowVariant {
   int M;
   int rows_per_block;
@@ -122,7 +123,7 @@ struct RowVariant {
   RowInvFn inv[4];
   RowFwdTabFn fwd_tab;   // null unless built for window tables (FP32 envelopes only)
   RowInvTabFn inv_tab;
-  RowFwdDenseFn fwd_dense;   // null unless built for the dense mode (FP32 envelopes only)
+  RowFwdDenseFn fwd_dense;   // null unless built for the dense mode
   RowInvDenseFn inv_dense;
 };
 // the dense-mode variants live in their own translation unit (kernels_rows_dense.cu)

@@ -433,17 +433,18 @@ template <typename T, bool PRED> struct AccumulateAbs {
   }
 };
 
-// Dense mode on a compile-time FFT (FP32 envelopes): the weights of the
+// Dense mode on a compile-time FFT (FP32 arithmetic, envelopes stored as
+// EnvKind E): the weights of the
 // integer-product / table path (c eps wherever the window vanishes, the band
 // spanning the one-sided spectrum through hb).  ABS: tiles with the carrier
 // and the floor, bins at their own positions (above); otherwise the band at
 // baseband with the carrier e^{+2 pi i k_c n / M} from the plan's M-point
 // table on store (its conjugate on load) when remod is set.  tws holds the
 // variant's stage twiddles, twM the plan's M-point table.
-template <class Eng, bool ABS>
+template <class Eng, bool ABS, int E>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
     k_rows_forward_sd(const RowDev<float>* __restrict__ rows, int n_rows, int64_t Nr, const float2* __restrict__ X,
-                      float2* __restrict__ y, int64_t n_units, const float2* __restrict__ tws,
+                      typename Env<float2, E>::S* __restrict__ y, int64_t n_units, const float2* __restrict__ tws,
                       const float* __restrict__ wtab, const float2* __restrict__ twM, int remod) {
   extern __shared__ __align__(16) unsigned char smraw[];
   float2* sm = reinterpret_cast<float2*>(smraw);
@@ -455,18 +456,19 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
   const RowCtx<float, false> rc = row_ctx<float, false>(rows, row, M, Nr, valid, false, wtab);
   if constexpr (ABS) {
     LoadSpectrumAbs<float> ld{X + seg * Nr, rc, valid ? (int)(Nr - 1) : -1};
-    StoreEnvelope<float2, ENV_F32> stv{y + (valid ? unit : 0) * M, valid};
+    StoreEnvelope<float2, E> stv{y + (valid ? unit : 0) * M, valid};
     Eng().template run<+1>(sm, tws, ld, stv);
   } else {
     LoadBand<float, false> ld{X + seg * Nr, rc};
-    StoreEnvelopeRT<float2, ENV_F32> stv{y + (valid ? unit : 0) * M, valid, remod, rc.kc % M, M, twM};
+    StoreEnvelopeRT<float2, E> stv{y + (valid ? unit : 0) * M, valid, remod, rc.kc % M, M, twM};
     Eng().template run<+1>(sm, tws, ld, stv);
   }
 }
-template <class Eng, bool ABS>
+template <class Eng, bool ABS, int E>
 __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
     k_rows_inverse_sd(const RowDev<float>* __restrict__ rows, const int* __restrict__ row_list, int n_sel, int n_rows,
-                      int64_t Nr, const float2* __restrict__ y, float2* __restrict__ A, int64_t n_units,
+                      int64_t Nr, const typename Env<float2, E>::S* __restrict__ y, float2* __restrict__ A,
+                      int64_t n_units,
                       const float2* __restrict__ tws, const float* __restrict__ wtab, const float2* __restrict__ twM,
                       int remod) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -478,11 +480,11 @@ __global__ void __launch_bounds__(Eng::NT, Eng::MINB)
   const int row = valid ? row_list[unit - seg * n_sel] : 0;
   const RowCtx<float, false> rc = row_ctx<float, false>(rows, row, M, Nr, valid, true, wtab);
   if constexpr (ABS) {
-    LoadEnvelope<float2, ENV_F32> ld{y + (seg * n_rows + row) * M, valid};
+    LoadEnvelope<float2, E> ld{y + (seg * n_rows + row) * M, valid};
     AccumulateAbs<float, Eng::PRED_RED> acc{A + seg * Nr, rc, valid ? (int)(Nr - 1) : -1};
     Eng().template run<-1>(sm, tws, ld, acc);
   } else {
-    LoadEnvelopeRT<float2, ENV_F32> ld{y + (seg * n_rows + row) * M, valid, remod, rc.kc % M, M, twM};
+    LoadEnvelopeRT<float2, E> ld{y + (seg * n_rows + row) * M, valid, remod, rc.kc % M, M, twM};
     AccumulateBand<float, false, Eng::PRED_RED> acc{A + seg * Nr, rc};
     Eng().template run<-1>(sm, tws, ld, acc);
   }
@@ -537,43 +539,68 @@ cudaError_t inv_launch_tab(const RowDev<float>* rows, const int* row_list, int n
 }
 
 // mode: 0 baseband tiles, 1 baseband tiles with the carrier, 2 tiles spanning
-// the spectrum with the carrier (bins at their own positions)
-template <class Eng, bool ABS>
+// the spectrum with the carrier (bins at their own positions); env: EnvKind
+// of the stored envelopes (F32, BF16 or F16)
+template <class Eng, bool ABS, int E>
 cudaError_t fwd_launch_dense_k(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
                                const float2* tws, cudaStream_t st, const float* wtab, const float2* twM, int remod) {
   const int64_t units = B * n_rows;
   const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
   const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_forward_sd<Eng, ABS>, smem);
-  k_rows_forward_sd<Eng, ABS><<<(unsigned)blocks, Eng::NT, smem, st>>>(rows, n_rows, Nr, X, static_cast<float2*>(y),
-                                                                        units, tws, wtab, twM, remod);
+  allow_smem((const void*)k_rows_forward_sd<Eng, ABS, E>, smem);
+  k_rows_forward_sd<Eng, ABS, E><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, n_rows, Nr, X, static_cast<typename Env<float2, E>::S*>(y), units, tws, wtab, twM, remod);
   return cudaGetLastError();
+}
+template <class Eng, int E>
+cudaError_t fwd_launch_dense_e(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
+                               const float2* tws, cudaStream_t st, const float* wtab, const float2* twM, int mode) {
+  return mode == 2 ? fwd_launch_dense_k<Eng, true, E>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, 0)
+                   : fwd_launch_dense_k<Eng, false, E>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, mode);
 }
 template <class Eng>
 cudaError_t fwd_launch_dense(const RowDev<float>* rows, int n_rows, int64_t Nr, const float2* X, void* y, int64_t B,
-                             const float2* tws, cudaStream_t st, const float* wtab, const float2* twM, int mode) {
-  return mode == 2 ? fwd_launch_dense_k<Eng, true>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, 0)
-                   : fwd_launch_dense_k<Eng, false>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, mode);
+                             const float2* tws, cudaStream_t st, const float* wtab, const float2* twM, int mode,
+                             int env) {
+  switch (env) {
+    case ENV_BF16: return fwd_launch_dense_e<Eng, ENV_BF16>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, mode);
+    case ENV_F16: return fwd_launch_dense_e<Eng, ENV_F16>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, mode);
+    default: return fwd_launch_dense_e<Eng, ENV_F32>(rows, n_rows, Nr, X, y, B, tws, st, wtab, twM, mode);
+  }
 }
-template <class Eng, bool ABS>
+template <class Eng, bool ABS, int E>
 cudaError_t inv_launch_dense_k(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
                                const void* y, float2* A, int64_t B, const float2* tws, cudaStream_t st,
                                const float* wtab, const float2* twM, int remod) {
   const int64_t units = B * n_sel;
   const int64_t blocks = (units + (1 << Eng::NBS) - 1) >> Eng::NBS;
   const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_inverse_sd<Eng, ABS>, smem);
-  k_rows_inverse_sd<Eng, ABS><<<(unsigned)blocks, Eng::NT, smem, st>>>(
-      rows, row_list, n_sel, n_rows, Nr, static_cast<const float2*>(y), A, units, tws, wtab, twM, remod);
+  allow_smem((const void*)k_rows_inverse_sd<Eng, ABS, E>, smem);
+  k_rows_inverse_sd<Eng, ABS, E><<<(unsigned)blocks, Eng::NT, smem, st>>>(
+      rows, row_list, n_sel, n_rows, Nr, static_cast<const typename Env<float2, E>::S*>(y), A, units, tws, wtab, twM,
+      remod);
   return cudaGetLastError();
+}
+template <class Eng, int E>
+cudaError_t inv_launch_dense_e(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
+                               const void* y, float2* A, int64_t B, const float2* tws, cudaStream_t st,
+                               const float* wtab, const float2* twM, int mode) {
+  return mode == 2
+             ? inv_launch_dense_k<Eng, true, E>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM, 0)
+             : inv_launch_dense_k<Eng, false, E>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM, mode);
 }
 template <class Eng>
 cudaError_t inv_launch_dense(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
                              const void* y, float2* A, int64_t B, const float2* tws, cudaStream_t st,
-                             const float* wtab, const float2* twM, int mode) {
-  return mode == 2 ? inv_launch_dense_k<Eng, true>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM, 0)
-                   : inv_launch_dense_k<Eng, false>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM,
-                                                    mode);
+                             const float* wtab, const float2* twM, int mode, int env) {
+  switch (env) {
+    case ENV_BF16:
+      return inv_launch_dense_e<Eng, ENV_BF16>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM, mode);
+    case ENV_F16:
+      return inv_launch_dense_e<Eng, ENV_F16>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM, mode);
+    default:
+      return inv_launch_dense_e<Eng, ENV_F32>(rows, row_list, n_sel, n_rows, Nr, y, A, B, tws, st, wtab, twM, mode);
+  }
 }
 
 template <class Eng> RowVariant make_variant(const char* name) {

@@ -186,7 +186,7 @@ def test_dense_mode_options():
     names = [qtam.qtam_variant_describe(v)["name"] for v in vs[1:]]
     assert all(n.startswith("4320:") for n in names)
     assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, n_out=4800, device=-1).handle) == [-1]
-    assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, envelope="bf16", device=-1).handle) == [-1]
+    assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, envelope="bf16", device=-1).handle) == vs
     assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, compute="f64", device=-1).handle) == [-1]
     r = qtam.Plan(*base, remodulate=True, n_out=4320, device=-1)     # carrier alone: dense kernels too
     assert len(qtam.qtam_plan_variants(r.handle)) == 4

@@ -27,9 +27,9 @@ CFGS = [
 ]
 
 
-def _make(c, compute, eps, remod, window="bisquare", n_out=0):
+def _make(c, compute, eps, remod, window="bisquare", n_out=0, envelope=None):
     p = qtam.Plan(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], compute=compute, stopband_eps=eps,
-                  remodulate=remod, window=window, n_out=n_out, device=0)
+                  remodulate=remod, window=window, n_out=n_out, envelope=envelope, device=0)
     g = O.geometry(c["fs"], c["N"], c["qs"], c["fmin"], c["fmax"], c["K"], stopband_eps=eps, remodulate=remod,
                    window=window, n_out=n_out)
     assert p.M == g.M and p.M >= g.Nr
@@ -88,6 +88,28 @@ def test_dense_compile_time_variants_match_oracle(eps, remod, window):
             assert _rel(Y[b], refs[b]) < 1e-6, v
             assert np.max(np.abs(Y[b] - refs[b])) <= 1e-5 * np.max(np.abs(refs[b])), v
             assert _rel(xh[b], projs[b]) < 1e-5, v
+
+
+@pytest.mark.parametrize("env", ["bf16", "f16"])
+def test_dense_16bit_envelopes_on_compile_time_variants(env):
+    """Dense tiles (floor and carrier) stored as BF16 / FP16 by the dense
+    variants, against the oracle at 16-bit storage accuracy: forward 1e-2
+    (BF16 keeps 8 significand bits, u = 2e-3; FP16 11 bits), the canonical
+    inverse of the stored tiles 2e-2 of the projection."""
+    c = CFGS[1]
+    p, g = _make(c, "f32", 1e-3, True, envelope=env)
+    assert p.info["row_variant"] >= 0
+    B = 2
+    x = np.stack([synth.glitchy_segment(720 + b, c["N"], c["fs"], chirp=True) for b in range(B)]).astype(np.float32)
+    y = p.forward(torch.from_numpy(x).cuda())
+    torch.cuda.synchronize()
+    a = y.float().cpu().numpy().astype(np.float64)
+    Y = a[..., 0] + 1j * a[..., 1]
+    xh = p.inverse(y).cpu().numpy().astype(np.float64)
+    for b in range(B):
+        ref = O.forward(g, x[b].astype(np.float64))
+        assert _rel(Y[b], ref) < 1e-2
+        assert _rel(xh[b], O.projection(g, x[b].astype(np.float64), tau=p.info["p_floor_rel"])) < 2e-2
 
 
 @pytest.mark.parametrize("remod", [False, True])
