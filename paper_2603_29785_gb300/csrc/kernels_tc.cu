@@ -137,27 +137,64 @@ __device__ __forceinline__ uint32_t pack_bf16(float a, float b) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// Per-row metadata of a pair (a four-slot ring in shared memory, filled two
+// pairs ahead by threads 0 and 1): the unit's validity and envelope offset
+// and the band parameters, so that the band gather (forward), the envelope
+// loads and the accumulation (inverse) start without dependent reads of the
+// row list and the row table.
+struct TcMeta {
+  long long yoff;   // (seg * n_rows + row) * M (forward: 0), or -1 when the pair has no such unit
+  long long aoff;   // seg * Nr + k_c: the row's centre bin in the spectrum
+  int h, woff, dhi, mlo;
+  float kw, cw;     // kw and c of the direction (forward kw_fwd, c_fwd; inverse kw_inv, c_inv)
+};
+
+// the row-list read of unit (pair pk, row r): first step of a metadata fill
+__device__ __forceinline__ bool tc_meta_unit(int64_t pk, int r, int64_t n_pairs, int64_t n_units, int n_sel,
+                                             const int* __restrict__ row_list, int64_t& seg, int& row) {
+  const int64_t u = 2 * pk + r;
+  if (pk >= n_pairs || u >= n_units) return false;
+  seg = u / n_sel;
+  row = row_list[u - seg * n_sel];
+  return true;
+}
+__device__ __forceinline__ TcMeta tc_meta_make(bool valid, int64_t seg, int row, const RowDev<float>& rd, int n_rows,
+                                               int64_t Nr, bool inv) {
+  TcMeta m;
+  m.yoff = valid ? (inv ? (seg * n_rows + row) * (int64_t)kTcM : 0) : -1;
+  m.aoff = seg * Nr + rd.kc;
+  m.h = rd.h;
+  m.woff = rd.woff;
+  m.dhi = (int)min((int64_t)rd.h, Nr - 1 - rd.kc);
+  m.mlo = kTcM + max(-rd.h, -rd.kc);
+  m.kw = inv ? rd.kw_inv : rd.kw_fwd;
+  m.cw = inv ? rd.c_inv : rd.c_fwd;
+  return m;
+}
+// the forward's unit (pair pk, row r): segment and row without a row list
+__device__ __forceinline__ bool tc_meta_unit_fwd(int64_t pk, int r, int64_t n_pairs, int64_t n_units, int n_rows,
+                                                 int64_t& seg, int& row) {
+  const int64_t u = 2 * pk + r;
+  if (pk >= n_pairs || u >= n_units) return false;
+  seg = u / n_rows;
+  row = (int)(u - seg * n_rows);
+  return true;
+}
+
 // Band gather + window of one pair of rows into Z (GEMM A's B operand,
 // [256 c = 128 r + j2][128 k = Re j1 | Im j1]).  Thread (r, j2, h) =
 // ((tid >> 7) & 1, tid & 127, tid >> 8) loads Z[r][128 j1 + j2] for j1 in
 // 32 h .. 32 h + 31: a warp's loads are 32 consecutive bins, its 16-byte
 // stores one core-matrix row each.
-__device__ __forceinline__ void tc_fill_z(unsigned char* sZ, int64_t pr, int64_t n_units, int n_rows, int64_t Nr,
-                                          const RowDev<float>* __restrict__ rows, const float2* __restrict__ X,
+__device__ __forceinline__ void tc_fill_z(unsigned char* sZ, const TcMeta* meta, const float2* __restrict__ X,
                                           const float* __restrict__ wtab) {
   const int tid = threadIdx.x;
   const int r = (tid >> 7) & 1, j2 = tid & 127, h0 = 4 * (tid >> 8);
-  const int64_t u = 2 * pr + r;
-  const bool valid = u < n_units;
-  const int64_t seg = valid ? u / n_rows : 0;
-  const int row = valid ? (int)(u - seg * n_rows) : 0;
-  const RowDev<float> rd = rows[row];
-  const int64_t nhalf = Nr - 1;
-  const int dhi = (int)min((int64_t)rd.h, nhalf - rd.kc);
-  const int dlo = (int)max((int64_t)-rd.h, (int64_t)-rd.kc);
-  const int mlo = kTcM + dlo;
-  const float2* Xs = X + seg * Nr + rd.kc;
-  const bool tab = wtab != nullptr && rd.woff >= 0;
+  const TcMeta m = meta[r];
+  const bool valid = m.yoff >= 0;
+  const int dhi = m.dhi, mlo = m.mlo;
+  const float2* Xs = X + m.aoff;
+  const bool tab = wtab != nullptr && m.woff >= 0;
   const unsigned c = 128u * r + j2;
 #pragma unroll 2
   for (int o = h0; o < h0 + 4; ++o) {
@@ -176,12 +213,12 @@ __device__ __forceinline__ void tc_fill_z(unsigned char* sZ, int64_t pr, int64_t
       const int d = lo ? j : j - kTcM;
       float2 v = make_float2(0.f, 0.f);
       if (valid && (lo || hi)) v = Xs[d];
-      const int a = min(d < 0 ? -d : d, rd.h);
+      const int a = min(d < 0 ? -d : d, m.h);
       float w;
       if (tab) {
-        w = rd.c_fwd * wtab[rd.woff + a];
+        w = m.cw * wtab[m.woff + a];
       } else {
-        const float uu = (float)((rd.h - a) * (rd.h + a)) * rd.kw_fwd;
+        const float uu = (float)((m.h - a) * (m.h + a)) * m.kw;
         w = uu * uu;
       }
       re[e] = v.x * w;
@@ -231,6 +268,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __shared__ __align__(8) uint64_t mbarA, mbarB;
   __shared__ uint32_t tslot;
   __shared__ int abort_flag;
+  __shared__ TcMeta smeta[4][2];          // pair of iteration i in slot i & 3
   unsigned char* sA = sm;                 // DFT-64 block, [128 n][128 k] K-major (GEMM A's B)
   unsigned char* sGr = sm + 32768;        // [128 n2][128 j2]
   unsigned char* sGi = sm + 65536;
@@ -257,7 +295,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   constexpr float kAng = 6.28318530717958647692f / (float)kTcM;
   const int64_t n_pairs = (n_units + 1) >> 1;
   int64_t pr = blockIdx.x;
-  if (pr < n_pairs) tc_fill_z(sZ, pr, n_units, n_rows, Nr, rows, X, wtab);
+  if (tid < 4) {   // metadata of the first two pairs (iterations 0 and 1)
+    const int it = tid >> 1, r = tid & 1;
+    int64_t seg = 0;
+    int row = 0;
+    const bool ok = tc_meta_unit_fwd(pr + it * (int64_t)gridDim.x, r, n_pairs, n_units, n_rows, seg, row);
+    smeta[it][r] = tc_meta_make(ok, seg, row, rows[row], n_rows, Nr, false);
+  }
+  __syncthreads();
+  if (pr < n_pairs) tc_fill_z(sZ, smeta[0], X, wtab);
   tc::fence_smem_to_async();
   tc::fence_before_sync();
   __syncthreads();
@@ -269,7 +315,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   bool pendA = false, pendB = false;
   int64_t prev = -1;
 
-  for (; pr < n_pairs; pr += gridDim.x) {
+  for (int it = 0; pr < n_pairs; pr += gridDim.x, ++it) {
+    // metadata of the pair two iterations ahead: the row-table read now, the
+    // slot written after the twiddle
+    int64_t mseg = 0;
+    int mrow = 0;
+    bool mok = false;
+    RowDev<float> mrd;
+    if (tid < 2) {
+      mok = tc_meta_unit_fwd(pr + 2 * (int64_t)gridDim.x, tid, n_pairs, n_units, n_rows, mseg, mrow);
+      mrd = rows[mrow];
+    }
     // ---- GEMM A: D_r[tmem 128 r ..] = Z_r^T * DFT64^T, r = 0, 1 ----
     if (tid == 0) {
       const uint32_t idesc = tc::make_idesc_bf16(128, 128);
@@ -323,6 +379,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     // the second half of the previous pair's stores, before GEMM B overwrites the Y columns
     if (prev >= 0) tc_store_y<E>(tbase, prev, n_units, y, 1, 2);
+    if (tid < 2) smeta[(it + 2) & 3][tid] = tc_meta_make(mok, mseg, mrow, mrd, n_rows, Nr, false);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
@@ -349,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     pendB = true;
     // ... overlapped with the next pair's band gather (GEMM A has finished reading Z)
     const int64_t nx = pr + gridDim.x;
-    if (nx < n_pairs) tc_fill_z(sZ, nx, n_units, n_rows, Nr, rows, X, wtab);
+    if (nx < n_pairs) tc_fill_z(sZ, smeta[(it + 1) & 3], X, wtab);
     if (!tc::mbar_wait_bounded(&mbarB, phB, tc::kWaitCycles)) abort_flag = 1;
     tc::fence_smem_to_async();
     tc::fence_before_sync();
@@ -466,40 +523,6 @@ __device__ __forceinline__ void red_add_if(float2* p, float v0, float v1, bool o
 // 64 n2 .. + 7; the 8 lanes of a quarter warp take 8 consecutive n2 of one
 // octet, so their 16-byte stores fill one core matrix (no bank conflicts)
 // and each lane reads whole 32-byte sectors.
-// Per-row metadata of a pair (a four-slot ring in shared memory, filled two
-// pairs ahead by threads 0 and 1): the envelope row's offset (-1: no unit)
-// and the band parameters, so that the envelope loads and the accumulation
-// start without dependent reads of the row list and the row table.
-struct TcMeta {
-  long long yoff;   // (seg * n_rows + row) * M, or -1
-  long long aoff;   // seg * Nr + k_c
-  int h, woff, dhi, mlo;
-  float kw, cw;     // kw_inv, c_inv
-};
-
-// the row-list read of unit (pair pk, row r): first step of a metadata fill
-__device__ __forceinline__ bool tc_meta_unit(int64_t pk, int r, int64_t n_pairs, int64_t n_units, int n_sel,
-                                             const int* __restrict__ row_list, int64_t& seg, int& row) {
-  const int64_t u = 2 * pk + r;
-  if (pk >= n_pairs || u >= n_units) return false;
-  seg = u / n_sel;
-  row = row_list[u - seg * n_sel];
-  return true;
-}
-__device__ __forceinline__ TcMeta tc_meta_make(bool valid, int64_t seg, int row, const RowDev<float>& rd, int n_rows,
-                                               int64_t Nr) {
-  TcMeta m;
-  m.yoff = valid ? (seg * n_rows + row) * (int64_t)kTcM : -1;
-  m.aoff = seg * Nr + rd.kc;
-  m.h = rd.h;
-  m.woff = rd.woff;
-  m.dhi = (int)min((int64_t)rd.h, Nr - 1 - rd.kc);
-  m.mlo = kTcM + max(-rd.h, -rd.kc);
-  m.kw = rd.kw_inv;
-  m.cw = rd.c_inv;
-  return m;
-}
-
 template <int E>
 __device__ __forceinline__ void tc_load_row(const typename TcEnv<E>::S* yr, typename TcLoad<E>::Raw (&raw)[2]) {
   if (!yr) return;
@@ -608,7 +631,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     int64_t seg = 0;
     int row = 0;
     const bool ok = tc_meta_unit(pr + it * (int64_t)gridDim.x, r, n_pairs, n_units, n_sel, row_list, seg, row);
-    smeta[it][r] = tc_meta_make(ok, seg, row, rows[ok ? row : 0], n_rows, Nr);
+    smeta[it][r] = tc_meta_make(ok, seg, row, rows[ok ? row : 0], n_rows, Nr, true);
   }
   __syncthreads();
   typename TcLoad<E>::Raw raw[2];
@@ -714,7 +737,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
       }
     }
-    if (tid < 2) smeta[(it + 2) & 3][tid] = tc_meta_make(mok, mseg, mrow, mrd, n_rows, Nr);
+    if (tid < 2) smeta[(it + 2) & 3][tid] = tc_meta_make(mok, mseg, mrow, mrd, n_rows, Nr, true);
     tc::fence_smem_to_async();
     tc::fence_before_sync();
     __syncthreads();
