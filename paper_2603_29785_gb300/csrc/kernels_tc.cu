@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 // ---- tensor-core analysis DFT of the inverse rows (M = 8192) -----------------
 //
-// Inverse rows (steps b1-b2), two rows per CTA iteration.  The synthesis
+// Inverse rows (steps a5-a6), two rows per CTA iteration.  The synthesis
 // needs S[j] = sum_n y[n] e^{-2 pi i j n/8192} of each envelope row; with
 // n = n1 + 64 n2 and j = 128 j1 + j2 it factors into
 //   E[n1][j2]      = sum_n2 y[n1 + 64 n2] e^{-2 pi i j2 n2/128}   GEMM B' (tensor cores)
