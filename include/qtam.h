@@ -97,7 +97,8 @@ typedef struct {
   int32_t n_q;            /* 1 .. 64 */
   double f_min, f_max;    /* log grid f_k = f_min (f_max/f_min)^(k/(K-1)), endpoints included */
   int32_t rows_per_plane; /* K >= 1 */
-  int32_t window;         /* QTAM_WIN_*; non-bisquare windows run the runtime-engine kernels */
+  int32_t window;         /* QTAM_WIN_*; non-bisquare windows read a per-plan W' table (compile-time
+                             row variants with F32 envelopes, else the runtime engine) */
   int32_t norm;           /* QTAM_NORM_* */
   double q_width;         /* half-width h = floor(f T q_width / Q); <= 0 selects sqrt(11) */
   double max_window_hz;   /* 0: automatic clamp from the largest centre gap (App. A); > 0: manual */
