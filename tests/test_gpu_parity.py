@@ -457,3 +457,30 @@ def test_edge_batch_above_grid_y_limit():
         xb = x[b].astype(np.float64)
         assert rel(y[b].cpu().numpy().astype(np.complex128), O.forward(g, xb)) < FWD_FROB["f32"], b
         assert rel(xh[b].cpu().numpy().astype(np.float64), O.projection(g, xb, tau=tau)) < RT["f32"], b
+
+
+def test_edge_maximum_length():
+    """The largest accepted segment, N = 2^27 (9.1 hours at 4096 Hz: a long FFT
+    of 2^26 complex points), two segments so the second starts 2^27 samples
+    in; the manual clamp keeps every window at h = 2048 (M = 4320).  Every row
+    of both segments and the second segment's round trip against the
+    oracle."""
+    N = 2 ** 27
+    p = make(4096.0, N, (8.0,), 20.0, 1024.0, 8, max_window_hz=0.125)
+    g = geom_of(p)
+    assert p.N == N and p.M == g.M == 4320 and int(g.h.max()) == 2048
+    B = 2
+    x = np.stack([synth.white(70 + b, N) for b in range(B)]).astype(np.float32)
+    xd = dev(x)
+    y = p.forward(xd)
+    xh = p.inverse(y)
+    torch.cuda.synchronize()
+    Y = env_np(p, y)
+    for b in range(B):
+        X = O.spectrum(x[b].astype(np.float64))
+        for k in range(g.K):
+            ref = O.forward_row(g, X, 0, k)
+            assert rel(Y[b, 0, k], ref) < FWD_FROB["f32"], (b, k)
+        del X
+    xb = x[1].astype(np.float64)
+    assert rel(host(xh[1:])[0], O.projection(g, xb, tau=p.info["p_floor_rel"])) < RT["f32"]
