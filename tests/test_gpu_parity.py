@@ -484,3 +484,23 @@ def test_edge_maximum_length():
         del X
     xb = x[1].astype(np.float64)
     assert rel(host(xh[1:])[0], O.projection(g, xb, tau=p.info["p_floor_rel"])) < RT["f32"]
+
+
+def test_edge_one_bin_windows():
+    """Rows whose ideal half-width rounds to 0 get h = 1 (reading C3b): the
+    bisquare is then a single bin (W' = 1 at k_c, 0 at k_c +/- 1); three such
+    rows beside wider ones, M = 15."""
+    p = make(64.0, 256, (40.0,), 2.0, 20.0, 6)
+    g = geom_of(p)
+    assert [int(h) for h in g.h[0]] == [1, 1, 1, 2, 4, 6] and p.M == g.M == 15
+    B = 3
+    x = np.stack([synth.white(80 + b, g.N) for b in range(B)]).astype(np.float32)
+    y = p.forward(dev(x))
+    Yg = env_np(p, y)
+    xh = host(p.inverse(y)).astype(np.float64)
+    for b in range(B):
+        xb = x[b].astype(np.float64)
+        ref = O.forward(g, xb)
+        assert rel(Yg[b], ref) < FWD_FROB["f32"]
+        assert elem_ok(Yg[b], ref, FWD_ELEM["f32"])
+        assert rel(xh[b], O.projection(g, xb, tau=p.info["p_floor_rel"])) < RT["f32"]
