@@ -61,7 +61,10 @@ documented choice; the same list is kept in the design notes):
       after the stream origin has its envelopes multiplied by
       exp(-2 pi i k_c a / N), so every chunk is demodulated against the same
       time origin and the map is continuous across chunks (the inverse
-      multiplies by the conjugate).  The stream is preceded by
+      multiplies by the conjugate).  A remodulated tile (D1) already carries
+      its carrier exp(+2 pi i k_c n / M) on absolute time: a circular shift
+      of x by a samples only shifts its columns, so its re-reference factor
+      is 1.  The stream is preceded by
       2G zeros; map column c is time c N/M - G, and the streaming inverse
       (re-chunk the map the same way, keep each chunk's central H samples)
       returns sample s at time s - 2G.
@@ -483,7 +486,11 @@ def stream_layout(g: Geometry, hop: int):
 def stream_phase(g: Geometry, a: int) -> np.ndarray:
     """[P, K] factors exp(-2 pi i k_c a / N) that re-reference the envelopes of a
     chunk starting at stream sample a to the stream origin (k_c a reduced mod N
-    in integers first)."""
+    in integers first); 1 for remodulated tiles, whose carrier
+    exp(+2 pi i k_c n / M) already refers column n to absolute time
+    (reading S1)."""
+    if g.remodulate:
+        return np.ones(g.kc.shape, dtype=np.complex128)
     m = np.mod(g.kc.astype(np.int64) * int(a), g.N)
     return np.exp(-2j * np.pi * m / g.N)
 

@@ -452,9 +452,9 @@ def test_composite_bank_planes_are_single_window_transforms():
 
 
 # --------------------------------------------------------------------------- streaming (reading S1)
-def _stream_geom():
+def _stream_geom(remodulate=False):
     # N = 1024 at 256 Hz, M = 96 (gcd 32 -> quantum 32 samples = 3 columns)
-    return O.geometry(256.0, 1024, (6.0, 12.0), 2.0, 100.0, 20, n_out=96)
+    return O.geometry(256.0, 1024, (6.0, 12.0), 2.0, 100.0, 20, n_out=96, remodulate=remodulate)
 
 
 def test_stream_layout_rules():
@@ -467,12 +467,15 @@ def test_stream_layout_rules():
             O.stream_layout(g, bad)
 
 
-def test_stream_of_a_periodic_signal_tiles_the_circular_transform():
+@pytest.mark.parametrize("remodulate", [False, True])
+def test_stream_of_a_periodic_signal_tiles_the_circular_transform(remodulate):
     """A stream repeating one segment x0 is, away from the zero prefix, the
     segment's circular transform tiled with the guard offset: map column c equals
     Y0 column (c - Gm) mod M, and the streaming inverse returns the projection
-    of x0 delayed by 2G (shift invariance in whole columns, App. C)."""
-    g = _stream_geom()
+    of x0 delayed by 2G (shift invariance in whole columns, App. C).  For
+    remodulated tiles the same holds with no re-reference phase, since their
+    carrier already refers each column to absolute time."""
+    g = _stream_geom(remodulate)
     hop = 512
     G, Hn, Gm = O.stream_layout(g, hop)
     x0 = _rand_x(g.N, 51)
