@@ -1,6 +1,7 @@
 """Plant plausible mistakes in the oracle (on the CPU) and check that the pins
 catch every one of them: a wrong sign, a dropped scale, an off-by-one shift,
-a wrong window exponent or normalisation, a wrong synthesis scale."""
+a wrong window exponent or normalisation, a wrong synthesis scale, a wrong
+stream phase or crop, a conjugated carrier."""
 import math
 
 import numpy as np
@@ -20,7 +21,8 @@ PIN_TESTS = [
     lambda gd: pins.test_bisquare_shape_and_moments(),
     lambda gd: pins.test_geometry_hand_derivations(gd),
     lambda gd: pins.test_grid_and_widths_follow_formulas(),
-    lambda gd: pins.test_stream_of_a_periodic_signal_tiles_the_circular_transform(),
+    lambda gd: pins.test_stream_of_a_periodic_signal_tiles_the_circular_transform(False),
+    lambda gd: pins.test_stream_of_a_periodic_signal_tiles_the_circular_transform(True),
     lambda gd: pins.test_stream_layout_rules(),
     lambda gd: pins.test_remodulated_tile_is_the_unshifted_filtered_spectrum(),
     lambda gd: pins.test_single_tile_inverse_recovers_the_signal(True),
@@ -85,6 +87,11 @@ def _phase_wrong_sign(g, a):
     return np.conj(_orig_phase(g, a))
 
 
+def _phase_on_remodulated_tiles(g, a):
+    m = np.mod(g.kc.astype(np.int64) * int(a), g.N)
+    return np.exp(-2j * np.pi * m / g.N)     # the demodulated tiles' factor, whatever the plan
+
+
 def _layout_crop_off_by_one(g, hop):
     G, Hn, Gm = _orig_layout(g, hop)
     return G, Hn, Gm + 1
@@ -99,6 +106,7 @@ MUTANTS = {
     "synthesis scale sqrt(M/N)": ("accumulate", _acc_wrong_scale),
     "synthesis of conj(Y)": ("accumulate", _acc_conj),
     "stream phase conjugated": ("stream_phase", _phase_wrong_sign),
+    "stream phase on remodulated tiles": ("stream_phase", _phase_on_remodulated_tiles),
     "stream crop one column late": ("stream_layout", _layout_crop_off_by_one),
     "remodulation with the conjugate carrier": ("carrier", _carrier_conj),
 }
