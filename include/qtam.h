@@ -163,6 +163,8 @@ typedef struct {
                                      the tensor-core short DFT it serves only an inverse of
                                      envelopes that are not 16-byte aligned */
   int32_t short_dft;              /* QTAM_SHORT_DFT_* engine of the envelope stage */
+  double stopband_eps;            /* dense mode floor (0: off) */
+  int32_t remodulate;             /* 1: envelopes carry the carrier exp(+2 pi i k_c n / M) */
 } qtam_plan_info_t;
 
 /* Fill *d with defaults: bisquare, L2 norm, q_width sqrt(11), automatic clamp
@@ -323,7 +325,9 @@ QTAM_API qtam_status qtam_forward_noalloc(qtam_plan_t plan, const void* x, int64
  * boundaries coincide.  A chunk starting a samples after the stream origin
  * has its envelope rows multiplied by exp(-2 pi i k_c a / N), so every chunk
  * is demodulated against the same time origin and the map is continuous
- * across chunks.  The stream starts after 2G zero samples: map column c is
+ * across chunks.  A remodulated plan's tiles already carry their carrier on
+ * absolute time (a shift of the input only shifts their columns), so their
+ * factor is 1.  The stream starts after 2G zero samples: map column c is
  * time c*N/M - G (forward delay G), and the streaming inverse returns sample
  * s at time s - 2G (a further G).
  *

@@ -942,6 +942,8 @@ qtam_status qtam_plan_info(qtam_plan_t pl, qtam_plan_info_t* o) {
   o->device_bytes = (int64_t)pl->device_bytes;
   o->row_variant = pl->rc.variant;
   o->short_dft = pl->rc.tensor ? QTAM_SHORT_DFT_TENSOR : QTAM_SHORT_DFT_CUDA;
+  o->stopband_eps = pl->eps;
+  o->remodulate = pl->remod;
   return QTAM_OK;
 }
 

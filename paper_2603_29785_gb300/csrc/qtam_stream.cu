@@ -310,7 +310,10 @@ qtam_status qtam_stream_create(qtam_plan_t plan, int64_t hop, int64_t max_chunks
     free_stream(s);
     return st;
   }
-  for (int r = 0; r < R; ++r) kc[r] = (int)kc64[r];
+  // the chunk re-reference exp(-/+ 2 pi i k_c a / N) is computed from these
+  // centres; remodulated tiles already refer their columns to absolute time,
+  // so their factor is 1 (centre 0)
+  for (int r = 0; r < R; ++r) kc[r] = info.remodulate ? 0 : (int)kc64[r];
   size_t wsb = 0;
   qtam_workspace_size(plan, max_chunks, &wsb);
   s->wsb = wsb;

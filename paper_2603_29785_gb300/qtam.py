@@ -73,7 +73,7 @@ class qtam_plan_info_t(ctypes.Structure):
         ("fft_n1", ctypes.c_int32), ("fft_n2", ctypes.c_int32), ("envelope_bytes_per_segment", ctypes.c_int64),
         ("band_bins", ctypes.c_int64), ("p_floor_rel", ctypes.c_double), ("kappa", ctypes.c_double),
         ("kept_bins", ctypes.c_int64), ("device_bytes", ctypes.c_int64), ("row_variant", ctypes.c_int32),
-        ("short_dft", ctypes.c_int32),
+        ("short_dft", ctypes.c_int32), ("stopband_eps", ctypes.c_double), ("remodulate", ctypes.c_int32),
     ]
 
 

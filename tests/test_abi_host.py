@@ -180,6 +180,7 @@ def test_dense_mode_options():
     base = (4096.0, 8192, (8.0,), 20.0, 2048.0, 32)
     p = qtam.Plan(*base, stopband_eps=1e-6, p_floor_rel=0.0, device=-1)
     assert p.M == 4320 and p.info["max_window"] == 4097            # smallest 2^a 3^b 5^c >= N/2 + 1
+    assert p.info["stopband_eps"] == 1e-6 and p.info["remodulate"] == 0
     assert p.info["kept_bins"] == 4097 and p.info["band_bins"] == 32 * 4097   # P > 0 on every bin
     vs = qtam.qtam_plan_variants(p.handle)                          # runtime engine + the dense variants
     assert vs[0] == -1 and len(vs) == 4 and p.info["row_variant"] == vs[1]
@@ -189,6 +190,7 @@ def test_dense_mode_options():
     assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, envelope="bf16", device=-1).handle) == vs
     assert qtam.qtam_plan_variants(qtam.Plan(*base, stopband_eps=1e-6, compute="f64", device=-1).handle) == [-1]
     r = qtam.Plan(*base, remodulate=True, n_out=4320, device=-1)     # carrier alone: dense kernels too
+    assert r.info["remodulate"] == 1 and r.info["stopband_eps"] == 0.0
     assert len(qtam.qtam_plan_variants(r.handle)) == 4
     assert _err(lambda: qtam.Plan(*base, stopband_eps=1e-6, n_out=4000, device=-1)) == 3    # aliasing
     assert _err(lambda: qtam.Plan(*base, stopband_eps=-1.0, device=-1)) == 1
