@@ -39,6 +39,58 @@ template <typename V> __device__ __forceinline__ V cmul(V a, V b) {
   return mk<V>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 template <typename V> __device__ __forceinline__ V cscale(V a, decltype(V::x) s) { return mk<V>(a.x * s, a.y * s); }
+
+// ---------------------------------------------------------------------------
+// component-wise arithmetic of the butterflies: for float2 one packed FP32x2
+// instruction (sm_100 family `add/sub/mul/fma.f32x2`) does both components;
+// double2 stays scalar.  add / sub / mul carry no rounding modifier, so the
+// assembler may still contract a multiply feeding an add, as for scalar code.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float2 padd(float2 a, float2 b) {
+  float2 r;
+  asm("{ .reg .b64 x, y, z; mov.b64 x, {%2, %3}; mov.b64 y, {%4, %5}; add.f32x2 z, x, y; mov.b64 {%0, %1}, z; }"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 psub(float2 a, float2 b) {
+  float2 r;
+  asm("{ .reg .b64 x, y, z; mov.b64 x, {%2, %3}; mov.b64 y, {%4, %5}; sub.f32x2 z, x, y; mov.b64 {%0, %1}, z; }"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+__device__ __forceinline__ float2 pmul(float2 a, float2 b) {
+  float2 r;
+  asm("{ .reg .b64 x, y, z; mov.b64 x, {%2, %3}; mov.b64 y, {%4, %5}; mul.f32x2 z, x, y; mov.b64 {%0, %1}, z; }"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+  return r;
+}
+// a * b + c
+__device__ __forceinline__ float2 pfma(float2 a, float2 b, float2 c) {
+  float2 r;
+  asm("{ .reg .b64 x, y, z, w; mov.b64 x, {%2, %3}; mov.b64 y, {%4, %5}; mov.b64 z, {%6, %7}; "
+      "fma.rn.f32x2 w, x, y, z; mov.b64 {%0, %1}, w; }"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return r;
+}
+__device__ __forceinline__ float2 vadd(float2 a, float2 b) { return padd(a, b); }
+__device__ __forceinline__ float2 vsub(float2 a, float2 b) { return psub(a, b); }
+// a k + b, k real
+__device__ __forceinline__ float2 vfmak(float2 a, float k, float2 b) { return pfma(a, make_float2(k, k), b); }
+__device__ __forceinline__ float2 vscalek(float2 a, float k) { return pmul(a, make_float2(k, k)); }
+__device__ __forceinline__ double2 vadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 vsub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 vfmak(double2 a, double k, double2 b) {
+  return make_double2(fma(a.x, k, b.x), fma(a.y, k, b.y));
+}
+__device__ __forceinline__ double2 vscalek(double2 a, double k) { return make_double2(a.x * k, a.y * k); }
+// a + S i b (the quarter turn is a swap: scalar)
+template <int S, typename V> __device__ __forceinline__ V add_si(V a, V b) {
+  return S > 0 ? mk<V>(a.x - b.y, a.y + b.x) : mk<V>(a.x + b.y, a.y - b.x);
+}
 template <typename V> __device__ __forceinline__ V cconj(V a) { return mk<V>(a.x, -a.y); }
 // multiply by S*i (S = +1 or -1)
 template <int S, typename V> __device__ __forceinline__ V mul_si(V a) {
@@ -84,53 +136,56 @@ template <int R, int S> struct Dft;
 
 template <int S> struct Dft<2, S> {
   template <typename V> __device__ __forceinline__ static void run(V* a) {
-    V t = a[0];
-    a[0] = t + a[1];
-    a[1] = t - a[1];
+    const V t = a[0];
+    a[0] = vadd(t, a[1]);
+    a[1] = vsub(t, a[1]);
   }
 };
 
+// y1,2 = m +- i h d with m = a0 - (a1 + a2)/2, d = a1 - a2, h = S sin(2 pi/3)
 template <int S> struct Dft<3, S> {
   template <typename V> __device__ __forceinline__ static void run(V* a) {
     using T = decltype(V::x);
-    constexpr T h = (T)0.86602540378443864676;  // sin(2 pi/3)
-    V t = a[1] + a[2];
-    V d = a[1] - a[2];
-    V m = mk<V>(a[0].x - (T)0.5 * t.x, a[0].y - (T)0.5 * t.y);
-    V r = mul_si<S>(cscale(d, h));
-    a[0] = a[0] + t;
-    a[1] = m + r;
-    a[2] = m - r;
+    constexpr T h = (T)(S * 0.86602540378443864676);
+    const V t = vadd(a[1], a[2]);
+    const V d = vsub(a[1], a[2]);
+    const V m = vfmak(t, (T)-0.5, a[0]);
+    a[0] = vadd(a[0], t);
+    a[1] = mk<V>(m.x - h * d.y, m.y + h * d.x);
+    a[2] = mk<V>(m.x + h * d.y, m.y - h * d.x);
   }
 };
 
 template <int S> struct Dft<4, S> {
   template <typename V> __device__ __forceinline__ static void run(V* a) {
-    V s02 = a[0] + a[2], d02 = a[0] - a[2];
-    V s13 = a[1] + a[3], d13 = mul_si<S>(a[1] - a[3]);
-    a[0] = s02 + s13;
-    a[2] = s02 - s13;
-    a[1] = d02 + d13;
-    a[3] = d02 - d13;
+    const V s02 = vadd(a[0], a[2]), d02 = vsub(a[0], a[2]);
+    const V s13 = vadd(a[1], a[3]), t = vsub(a[1], a[3]);
+    a[0] = vadd(s02, s13);
+    a[2] = vsub(s02, s13);
+    a[1] = add_si<S>(d02, t);
+    a[3] = add_si<-S>(d02, t);
   }
 };
 
+// y1,4 = m1 +- i r1, y2,3 = m2 +- i r2 with t1 = a1 + a4, d1 = a1 - a4,
+// t2 = a2 + a3, d2 = a2 - a3, m1 = a0 + c1 t1 + c2 t2, m2 = a0 + c2 t1 + c1 t2,
+// r1 = s1 d1 + s2 d2, r2 = s2 d1 - s1 d2 (c_k = cos(2 pi k/5), s_k = S sin(2 pi k/5))
 template <int S> struct Dft<5, S> {
   template <typename V> __device__ __forceinline__ static void run(V* a) {
     using T = decltype(V::x);
     constexpr T c1 = (T)ce_cos2pi(1, 5), c2 = (T)ce_cos2pi(2, 5);
-    constexpr T s1 = (T)ce_sin2pi(1, 5), s2 = (T)ce_sin2pi(2, 5);
-    V t1 = a[1] + a[4], d1 = a[1] - a[4];
-    V t2 = a[2] + a[3], d2 = a[2] - a[3];
-    V m1 = mk<V>(a[0].x + c1 * t1.x + c2 * t2.x, a[0].y + c1 * t1.y + c2 * t2.y);
-    V m2 = mk<V>(a[0].x + c2 * t1.x + c1 * t2.x, a[0].y + c2 * t1.y + c1 * t2.y);
-    V r1 = mul_si<S>(mk<V>(s1 * d1.x + s2 * d2.x, s1 * d1.y + s2 * d2.y));
-    V r2 = mul_si<S>(mk<V>(s2 * d1.x - s1 * d2.x, s2 * d1.y - s1 * d2.y));
-    a[0] = a[0] + t1 + t2;
-    a[1] = m1 + r1;
-    a[4] = m1 - r1;
-    a[2] = m2 + r2;
-    a[3] = m2 - r2;
+    constexpr T s1 = (T)(S * ce_sin2pi(1, 5)), s2 = (T)(S * ce_sin2pi(2, 5));
+    const V t1 = vadd(a[1], a[4]), d1 = vsub(a[1], a[4]);
+    const V t2 = vadd(a[2], a[3]), d2 = vsub(a[2], a[3]);
+    const V m1 = vfmak(t2, c2, vfmak(t1, c1, a[0]));
+    const V m2 = vfmak(t2, c1, vfmak(t1, c2, a[0]));
+    const V r1 = vfmak(d1, s1, vscalek(d2, s2));
+    const V r2 = vfmak(d1, s2, vscalek(d2, -s1));
+    a[0] = vadd(vadd(a[0], t1), t2);
+    a[1] = add_si<1>(m1, r1);
+    a[4] = add_si<-1>(m1, r1);
+    a[2] = add_si<1>(m2, r2);
+    a[3] = add_si<-1>(m2, r2);
   }
 };
 

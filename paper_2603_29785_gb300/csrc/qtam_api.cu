@@ -368,14 +368,24 @@ bool choose_long(int64_t n, bool dbl, LongCfg& lc) {
 }
 
 // Build the stage twiddle tables of a compile-time radix sequence in FP64,
-// round to float once and upload them.
-qtam_status upload_stage_table(const int* r, int nst, void** dst, size_t& total) {
+// round to float once and upload them; `pair` writes each entry (c, s) as
+// (c, c, s, s), the layout of the row-pair kernels (one value per row lane).
+qtam_status upload_stage_table(const int* r, int nst, void** dst, size_t& total, bool pair = false) {
   size_t n = 0;
   stage_twiddles(r, nst, nullptr, &n);
   if (n == 0) n = 1;
   std::vector<double> d(2 * n, 0.0);
   stage_twiddles(r, nst, d.data(), &n);
-  std::vector<float> f(d.begin(), d.end());
+  std::vector<float> f;
+  if (pair) {
+    f.reserve(4 * n);
+    for (size_t t = 0; t < n; ++t) {
+      const float c = (float)d[2 * t], s = (float)d[2 * t + 1];
+      f.insert(f.end(), {c, c, s, s});
+    }
+  } else {
+    f.assign(d.begin(), d.end());
+  }
   return upload(dst, f.data(), f.size() * sizeof(float), total);
 }
 
@@ -493,7 +503,7 @@ template <typename T> qtam_status upload_tables(qtam_plan_s* pl) {
       const RowVariant* rv = row_variant(v);
       if (rv->M != pl->M) continue;
       void* p = nullptr;
-      if ((s = upload_stage_table(rv->r, rv->nst, &p, tot)) != QTAM_OK) return s;
+      if ((s = upload_stage_table(rv->r, rv->nst, &p, tot, rv->tw_pair != 0)) != QTAM_OK) return s;
       pl->variant_tw[v] = p;
     }
     int r[kMaxStages], nst = 0;
