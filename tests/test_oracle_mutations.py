@@ -1,7 +1,8 @@
 """Plant plausible mistakes in the oracle (on the CPU) and check that the pins
 catch every one of them: a wrong sign, a dropped scale, an off-by-one shift,
 a wrong window exponent or normalisation, a wrong synthesis scale, a wrong
-stream phase or crop, a conjugated carrier."""
+stream phase or crop, a conjugated carrier, a wrong Kaiser argument, a wrong
+frame-amplification formula."""
 import math
 
 import numpy as np
@@ -26,6 +27,8 @@ PIN_TESTS = [
     lambda gd: pins.test_stream_layout_rules(),
     lambda gd: pins.test_remodulated_tile_is_the_unshifted_filtered_spectrum(),
     lambda gd: pins.test_single_tile_inverse_recovers_the_signal(True),
+    lambda gd: pins.test_kaiser_window_integral_closed_form(),
+    lambda gd: pins.test_kappa_hand_case(),
 ]
 
 
@@ -72,6 +75,32 @@ def _acc_conj(g, Y, planes=None):
     return _orig_acc(g, np.conj(Y), planes)
 
 
+_orig_window_profile = O.window_profile
+
+
+def _kaiser_argument_without_sqrt(d, h, window="bisquare", param=0.0):
+    if window != "kaiser":
+        return _orig_window_profile(d, h, window, param)
+    u = np.abs(np.asarray(d, dtype=np.float64)) / float(h)
+    w = np.i0(float(param) * np.clip(1.0 - u * u, 0.0, None)) / np.i0(float(param))
+    return np.where(u <= 1.0, w, 0.0)
+
+
+_orig_kappa = O.kappa
+
+
+def _kappa_of_squared_windows(g, planes=None, tau=0.0):
+    # max W^2 / P instead of max W / P
+    planes = range(g.P) if planes is None else planes
+    Pf = O.frame_operator(g, planes)
+    Wmax = np.zeros(g.Nr)
+    for p in planes:
+        for k in range(g.K):
+            Wmax = np.maximum(Wmax, O.window(g, p, k))
+    keep = O.kept_bins(Pf, tau)
+    return float(np.max(Wmax[keep] ** 2 / Pf[keep]))
+
+
 _orig_carrier = O.carrier
 
 
@@ -109,6 +138,8 @@ MUTANTS = {
     "stream phase on remodulated tiles": ("stream_phase", _phase_on_remodulated_tiles),
     "stream crop one column late": ("stream_layout", _layout_crop_off_by_one),
     "remodulation with the conjugate carrier": ("carrier", _carrier_conj),
+    "Kaiser I0 argument beta (1 - u^2)": ("window_profile", _kaiser_argument_without_sqrt),
+    "kappa of squared windows": ("kappa", _kappa_of_squared_windows),
 }
 
 

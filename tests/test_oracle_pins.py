@@ -407,6 +407,32 @@ def test_window_family_special_cases_and_moments():
     assert w1 + w2 == pytest.approx(1.0, abs=2e-3)
 
 
+def test_kaiser_window_integral_closed_form():
+    """Kaiser window (App. A): int_{-1}^{1} I0(beta sqrt(1 - u^2)) du = 2 sinh(beta) / beta,
+    so the trapezoid sum of W'(d) = I0(beta sqrt(1 - (d/h)^2)) / I0(beta) over
+    |d| <= h, divided by h, tends to 2 sinh(beta) / (beta I0(beta)) with an
+    O(1/h^2) error.  Fixes the interior shape, not only the end points (an
+    argument beta (1 - u^2) misses it by 9-25 %)."""
+    h = 4000
+    d = np.arange(-h, h + 1)
+    for beta in (2.0, 6.0, 8.0):
+        w = O.window_profile(d, h, "kaiser", beta)
+        trap = (np.sum(w) - 0.5 * (w[0] + w[-1])) / h
+        closed = 2.0 * math.sinh(beta) / (beta * float(np.i0(beta)))
+        assert trap == pytest.approx(closed, rel=1e-7), beta
+
+
+def test_kappa_hand_case():
+    """kappa = max over kept bins of (max_k W_k) / P.  Two rows far apart, both
+    clamped to h = 3 (T = 1 s, manual clamp 7 Hz: h_max = floor(ceil(7) / 2)):
+    each kept bin sees one window, P = W^2 there, so kappa = 1 / min W over the
+    kept bins = 1 / (c W'(2)) with W'(2) = ((9 - 4) / 9)^2 = 25/81 (W'(3) = 0 is
+    not kept) and c = (sum W'^2)^(-1/2) = (6561 / 16003)^(1/2): kappa = sqrt(16003) / 25."""
+    g = O.geometry(4096.0, 4096, (8.0,), 100.0, 1000.0, 2, max_window_hz=7.0)
+    assert list(g.h.ravel()) == [3, 3] and list(g.kc.ravel()) == [100, 1000]
+    assert O.kappa(g) == pytest.approx(math.sqrt(16003.0) / 25.0, rel=1e-13)
+
+
 @pytest.mark.parametrize("window,param", [("hann", 0.0), ("kaiser", 6.0), ("tukey", 0.5), ("planck", 0.3)])
 def test_window_family_frame_identities(window, param):
     """App. C holds for any window: round trip = projection, frame energy identity."""
