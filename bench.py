@@ -41,6 +41,10 @@ def parse():
     ap.add_argument("--batch", type=int, default=64, help="segments per GPU per step")
     ap.add_argument("--impl", default="qtam", choices=["qtam", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the serving, batched and precision legs of the default line")
+    ap.add_argument("--serving-seconds", type=float, default=12.0,
+                    help="seconds of arrivals of the serving leg in the default line")
     ap.add_argument("--cpu-sample-segments", type=int, default=4)
     ap.add_argument("--variant", type=int, default=None,
                     help="row-kernel variant id (default: chosen by the autotuner)")
@@ -81,6 +85,15 @@ def dist_env():
 def make_inputs(seeds):
     from paper_2603_29785_gb300 import synth
     return np.stack([synth.coloured_chirp_segment(int(s), n=WORKLOAD["N"], fs=WORKLOAD["fs"]) for s in seeds])
+
+
+def hbm_peak_gbs():
+    """Measured HBM copy bandwidth of this machine's GPUs (GB/s) and its source."""
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        return float(peaks["hbm_gbs"]), "measured"
+    except (OSError, ValueError, KeyError):
+        return 6800.0, "fallback"
 
 
 # ---------------------------------------------------------------------------- clocks
@@ -316,6 +329,10 @@ def run_gpu(args, rank, world, local):
     torch.cuda.synchronize()
     stage_ms = np.zeros(4)
     total_ms = 0.0
+    step_ms = []
+    # the sampler runs from the timed loop through the e2e and per-segment
+    # legs (the GPU is busy throughout), so the record holds more than the one
+    # sample a ~25 ms loop would give at 50 ms intervals
     clocks = ClockSampler(local)
     if dist is not None:
         dist.barrier()
@@ -329,11 +346,11 @@ def run_gpu(args, rank, world, local):
         ev[4].synchronize()
         t = [ev[i].elapsed_time(ev[i + 1]) for i in range(4)]
         stage_ms += t
-        total_ms += ev[0].elapsed_time(ev[4])
+        step_ms.append(ev[0].elapsed_time(ev[4]))
+        total_ms += step_ms[-1]
     torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-    clk = clocks.stop()
     ms_per_step = reduce_max(total_ms / args.steps, dist, dev)
     samples_per_step = world * B * N
     value = samples_per_step / (ms_per_step * 1e-3) / 1e6
@@ -370,17 +387,13 @@ def run_gpu(args, rank, world, local):
         ev[4].synchronize()
         ps_ms += ev[0].elapsed_time(ev[4])
     ps_ms = reduce_max(ps_ms / args.steps, dist, dev)
+    clk = clocks.stop()
+    clk["window"] = "timed loop, e2e and per-segment legs"
     per_seg = {"value": round(samples_per_step / (ps_ms * 1e-3) / 1e6, 2), "unit": UNIT, "ms_per_step": round(ps_ms, 4),
                "path": "the same segments, one qtam_forward + qtam_inverse call pair per segment"}
 
     # ---- roofline of the dominant kernel (envelope kernel: writes B*P*K*M complex64) ----
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except (OSError, ValueError):
-        pass
-    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    hbm_peak, peak_src = hbm_peak_gbs()
     env_bytes = B * P * K * M * 8
     x_bytes = B * N * 4
     stage_bytes = [x_bytes, env_bytes, env_bytes, x_bytes]       # algorithmic HBM bytes per stage launch
@@ -417,7 +430,21 @@ def run_gpu(args, rank, world, local):
         # k_untangle_inverse, k_row_inverse, k_col_inverse (synthesis) -- as the ncu launch list shows
         "gpu_launches": 8 * args.steps,
         "clocks": clk,
+        # latency of one whole step (64 segments forward + inverse), over the timed steps
+        "latency": {"step_p50_ms": round(float(np.percentile(step_ms, 50)), 4),
+                    "step_p99_ms": round(float(np.percentile(step_ms, 99)), 4),
+                    "step_max_ms": round(float(np.max(step_ms)), 4)},
     }
+    if rank == 0 and world == 1 and not args.no_extras:
+        # the metric's p99 latency under load, and the batched and precision
+        # configurations, as extra keys of the same line
+        sv = serving_leg(local, args.serving_seconds)
+        line["serving"] = dict(sv["serving"], config=sv["config"], clocks=sv["clocks"])
+        line["latency"]["serving_p50_ms"] = sv["serving"]["p50_ms"]
+        line["latency"]["serving_p99_ms"] = sv["serving"]["p99_ms"]
+        bl = batched_leg(argparse.Namespace(steps=max(3, min(args.steps, 10)), warmup=3), local)
+        line["batched"] = bl
+        line["precision"] = precision_leg(argparse.Namespace(steps=max(3, min(args.steps, 10))), local, B)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         nseg = max(1, min(args.cpu_sample_segments, B))
         torch.cuda.synchronize()
@@ -443,12 +470,12 @@ def _clock_wrap(fn, local):
     return out, clk
 
 
-def run_batched(args, local):
+def batched_leg(args, local):
     """512 uneven segments (1-32 s, 4096/16384 Hz), Q {8,16,32} x 128 rows:
     forward + inverse of all segments captured as one CUDA graph, against the
     plain path (one forward + one inverse call per segment, no graph)."""
     import torch
-    from paper_2603_29785_gb300 import batch as qb, qtam
+    from paper_2603_29785_gb300 import batch as qb
     torch.cuda.set_device(local)
     segs, rates = qb.uneven_workload(512, seed=0)
     cache = qb.PlanCache((8.0, 16.0, 32.0), 20.0, 2048.0, 128, device=local)
@@ -500,20 +527,31 @@ def run_batched(args, local):
     e1.synchronize()
     ms_plain = e0.elapsed_time(e1) / reps
     bytes_alg = 2 * (ub.envelope_bytes + ub.samples * 4)
-    peak = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))).get("hbm_gbs", 6800.0)) \
-        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 6800.0
-    line = {"metric": "QTAM fwd+inv Msamples/s, uneven batch in one CUDA graph", "value": round(ub.samples / ms / 1e3, 2),
-            "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms, 4),
-            "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+    peak, src = hbm_peak_gbs()
+    gbs = bytes_alg / (ms * 1e-3) / 1e9
+    return {"value": round(ub.samples / ms / 1e3, 2), "unit": UNIT, "ms_per_step": round(ms, 4),
+            "steps": args.steps, "warmup": args.warmup,
             "config": {"workload": "512 segments, 1-32 s, half 4096 Hz / half 16384 Hz, Q {8,16,32} x 128 rows 20-2048 Hz",
-                       "groups": len(ub.groups), "graph_streams": 4, "samples": ub.samples, "envelope_bytes": ub.envelope_bytes,
-                       "l2": "inputs+envelopes (1.4 GB) larger than L2"},
-            "path_hbm_frac": round(bytes_alg / (ms * 1e-3) / 1e9 / peak, 4),
+                       "groups": len(ub.groups), "graph_streams": 4, "samples": ub.samples,
+                       "envelope_bytes": ub.envelope_bytes, "l2": "inputs+envelopes (1.4 GB) larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(gbs / peak, 4), "peak_source": src,
+                         "bytes": "2 x (envelopes + input samples) per replay: forward writes and inverse reads "
+                                  "every envelope, forward reads and inverse writes every sample"},
             "per_segment_plain_path": {"value": round(ub.samples / ms_plain / 1e3, 2), "ms_per_step": round(ms_plain, 3),
                                        "launches": "2 calls per segment, no graph"},
             "speedup_vs_plain": round(ms_plain / ms, 2),
-            "graph_one_stream": {"value": round(ub.samples / ms_one_stream / 1e3, 2), "ms_per_step": round(ms_one_stream, 4)},
+            "graph_one_stream": {"value": round(ub.samples / ms_one_stream / 1e3, 2),
+                                 "ms_per_step": round(ms_one_stream, 4)},
             "clocks": clk}
+
+
+def run_batched(args, local):
+    b = batched_leg(args, local)
+    line = {"metric": "QTAM fwd+inv Msamples/s, uneven batch in one CUDA graph", "value": b.pop("value"),
+            "unit": UNIT, "n_gpus": 1, "higher_is_better": True, "dtype": "f32", "data": "synthetic",
+            "path_hbm_frac": b["roofline"]["frac"]}
+    line.update(b)
     print(json.dumps(line), flush=True)
 
 
@@ -706,14 +744,14 @@ def run_bank(args, local):
     print(json.dumps(line), flush=True)
 
 
-def run_serving(args, local):
+def serving_leg(local, duration):
     """Poisson arrivals (200/s) of 3-channel 8 s @ 4096 Hz requests, Q in
     {8,16,32}, 20 % inverse of row-zeroed envelopes; 40 GB HBM budget."""
     import torch
     from paper_2603_29785_gb300 import serve
     torch.cuda.set_device(local)
     pool = [serve.make_request(i, 5000 + i) for i in range(256)]
-    arrivals = serve.poisson_arrivals(200.0, args.duration, seed=7)
+    arrivals = serve.poisson_arrivals(200.0, duration, seed=7)
     reqs = [serve.Request(i, pool[i % len(pool)].x, pool[i % len(pool)].q, pool[i % len(pool)].kind,
                           pool[i % len(pool)].row_gain) for i in range(len(arrivals))]
     ex = serve.GpuExecutor(slots=4, device=local)
@@ -722,16 +760,22 @@ def run_serving(args, local):
                      np.zeros(32), realtime=False)
     srv = serve.Server(ex, hbm_budget_bytes=40 * 2**30, max_batch_requests=32)
     st, clk = _clock_wrap(lambda: serve.run_stream(srv, reqs, arrivals), local)
-    line = {"metric": "QTAM serving p50/p99 latency (ms) and Msamples/s", "value": round(st["p99_ms"], 3),
-            "unit": "ms p99", "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "Poisson 200 req/s, 3 x 8 s @ 4096 Hz per request, Q {8,16,32} x 128 rows, "
-                                   "20 % inverse of row-zeroed envelopes", "duration_s": args.duration,
+    st["target_p99_ms"] = 100.0
+    return {"config": {"workload": "Poisson 200 req/s, 3 x 8 s @ 4096 Hz per request, Q {8,16,32} x 128 rows, "
+                                   "20 % inverse of row-zeroed envelopes", "duration_s": duration,
                        "hbm_budget_gb": 40, "streams": ex.slots, "max_batch_requests": 32},
             "serving": st, "clocks": clk}
+
+
+def run_serving(args, local):
+    sv = serving_leg(local, args.duration)
+    line = {"metric": "QTAM serving p50/p99 latency (ms) and Msamples/s", "value": round(sv["serving"]["p99_ms"], 3),
+            "unit": "ms p99", "higher_is_better": False, "n_gpus": 1, "dtype": "f32", "data": "synthetic"}
+    line.update(sv)
     print(json.dumps(line), flush=True)
 
 
-def run_precision(args, local):
+def precision_leg(args, local, B):
     """Precision sweep on the 64 s workload: envelope storage FP32 / BF16 / FP16
     at M = 4800 (CUDA-core FFTs), and at M = 8192 the CUDA-core runtime engine
     against the tensor-core short DFT (64 x 128 four-step on tcgen05, BF16
@@ -742,7 +786,6 @@ def run_precision(args, local):
     from oracle import qtam_oracle as O
     from paper_2603_29785_gb300 import qtam, tune as qtune
     torch.cuda.set_device(local)
-    B = args.batch
     W = WORKLOAD
     x_host = make_inputs(range(B))
     refs = {}
@@ -803,6 +846,10 @@ def run_precision(args, local):
                 "envelope_stage_ms": round(ms_env, 4), "accumulate_stage_ms": round(ms_acc, 4),
                 "envelope_stage_GB_s": round(B * p.info["envelope_bytes_per_segment"] / (ms_env * 1e-3) / 1e9, 1),
                 "envelope_bytes_per_segment": p.info["envelope_bytes_per_segment"]}
+        pk_hbm, _ = hbm_peak_gbs()
+        item["envelope_stage_hbm_frac"] = round(item["envelope_stage_GB_s"] / pk_hbm, 4)
+        item["accumulate_stage_hbm_frac"] = round(
+            B * p.info["envelope_bytes_per_segment"] / (ms_acc * 1e-3) / 1e9 / pk_hbm, 4)
         if sd == "tensor":
             # two tcgen05 GEMMs per pair of rows in each direction: 128x256x128 +
             # 4 x 128x128x128 multiply-adds
@@ -814,9 +861,14 @@ def run_precision(args, local):
                               "inverse_achieved_tflops": round(tfi, 1), "inverse_frac": round(tfi / pk, 4),
                               "peak_source": "measured" if "bf16_tflops" in peaks else "fallback"}
         out.append(item)
+    return out
+
+
+def run_precision(args, local):
+    out = precision_leg(args, local, args.batch)
     line = {"metric": "QTAM precision sweep: error vs FP64 oracle and Msamples/s per envelope dtype and short-DFT engine",
             "value": out[0]["msamples_per_s"], "unit": UNIT, "n_gpus": 1, "dtype": "f32 compute",
-            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "segments": B}, "precision": out}
+            "data": "synthetic", "config": {"workload": WORKLOAD_NAME, "segments": args.batch}, "precision": out}
     print(json.dumps(line), flush=True)
 
 

@@ -79,6 +79,25 @@ class Executor:
         raise NotImplementedError
 
 
+_ENV_BYTES = {"f32": 8, "f64": 16, "bf16": 4, "f16": 4}
+
+
+def batch_allocations(plan, kind: str, n_segments: int) -> dict:
+    """Device bytes one batch of `n_segments` allocates, per tensor: the input
+    samples, the envelopes, the long-FFT workspace (qtam_workspace_size), and
+    for an inverse the row gains and the reconstruction.  The executor charges
+    their sum against the HBM budget and allocates exactly these tensors."""
+    from . import qtam
+    B = int(n_segments)
+    out = {"x": B * plan.N * 4,
+           "y": B * plan.P * plan.K * plan.M * _ENV_BYTES[plan.envelope],
+           "workspace": qtam.qtam_workspace_size(plan.handle, B)}
+    if kind == "inverse":
+        out["gain"] = B * plan.P * plan.K * 4
+        out["xh"] = B * plan.N * 4
+    return out
+
+
 class GpuExecutor(Executor):
     """Runs batches with the library's C entry points on `slots` CUDA streams."""
 
@@ -95,7 +114,6 @@ class GpuExecutor(Executor):
         self.K = rows_per_plane
         self.f_min, self.f_max = f_min, f_max
         self.streams = [torch.cuda.Stream(device=device) for _ in range(slots)]
-        self.ws = [None] * slots
         # per-slot pinned staging (input samples, output samples or envelopes),
         # grown on demand and reused: a slot's buffers are free again once its
         # batch has been collected, and pinning per batch would cost milliseconds
@@ -114,17 +132,7 @@ class GpuExecutor(Executor):
 
     def nbytes(self, key, n_segments):
         fs, N, q, kind = key
-        p = self.plan(fs, N, q)
-        per = N * 4 + p.info["envelope_bytes_per_segment"] + (N * 4 + p.P * p.K * 4 if kind == "inverse" else 0)
-        return n_segments * per
-
-    def _workspace(self, slot, need):
-        t = self.torch
-        ws = self.ws[slot]
-        if ws is None or ws.numel() < need:
-            ws = t.empty(max(need, 256), dtype=t.uint8, device=f"cuda:{self.device}")
-            self.ws[slot] = ws
-        return ws
+        return sum(batch_allocations(self.plan(fs, N, q), kind, n_segments).values())
 
     def _pinned(self, pool, slot, shape, dtype):
         """A pinned host tensor of `shape` and `dtype` on the slot's reusable bytes."""
@@ -151,9 +159,12 @@ class GpuExecutor(Executor):
             xs[o:o + r.x.shape[0]] = r.x
             o += r.x.shape[0]
         with t.cuda.stream(st):
+            # every device tensor of the batch is allocated here, on the batch's
+            # stream, and released when the batch is collected: the bytes in
+            # flight are exactly what admission charged (batch_allocations)
             x = x_host.to(dev, non_blocking=True)
             y = p.envelope_tensor(B)
-            ws = self._workspace(slot, qtam.qtam_workspace_size(p.handle, B))
+            ws = t.empty(max(qtam.qtam_workspace_size(p.handle, B), 256), dtype=t.uint8, device=dev)
             qtam.qtam_forward(p.handle, x, B, y, ws, ws.numel(), st)
             if kind == "inverse":
                 g = np.concatenate([r.row_gain if r.row_gain is not None else np.ones((r.x.shape[0], p.K), np.float32)
@@ -164,13 +175,16 @@ class GpuExecutor(Executor):
                 qtam.qtam_inverse(p.handle, y, B, 0, xh, ws, ws.numel(), st)
                 out = self._pinned(self.pin_out, slot, (B, N), t.float32)
                 out.copy_(xh, non_blocking=True)
-                keep = (gain, y, xh)
+                keep = (x, y, ws, gain, xh)
             else:
                 out = self._pinned(self.pin_out, slot, tuple(y.shape), y.dtype)
                 out.copy_(y, non_blocking=True)
-                keep = (x, y)
+                keep = (x, y, ws)
             ev = t.cuda.Event()
             ev.record(st)
+        used = sum(v.numel() * v.element_size() for v in keep)
+        if used > batch.nbytes:
+            raise RuntimeError(f"batch allocated {used} device bytes, {batch.nbytes} were charged")
         batch.handle = (ev, out, keep)
 
     def poll(self, batch):

@@ -74,3 +74,20 @@ def test_tiny_budget_serialises_but_completes(requests):
     mix = [fresh(r) for r in requests[:5]]
     st = serve.run_stream(s, mix, np.zeros(len(mix)))
     assert st["completed"] + st["rejected"] == 5 and s.peak_bytes <= one * 1.5
+
+
+def test_batch_device_bytes_within_its_charge(requests):
+    """The bytes a batch holds on the device while in flight (input, envelopes,
+    long-FFT workspace, inverse gains and output) stay within what admission
+    charged for it (torch rounds each allocation up to 512 bytes)."""
+    ex = serve.GpuExecutor(slots=1)
+    for r in requests[:4]:
+        key = ex.key(r)
+        nb = ex.nbytes(key, r.x.shape[0])
+        torch.cuda.synchronize()
+        before = torch.cuda.memory_allocated()
+        b = serve.Batch(key, [fresh(r)], nb)
+        ex.launch(b, 0)
+        held = torch.cuda.memory_allocated() - before
+        ex.collect(b)
+        assert 0 < held <= nb + 5 * 512, (r.kind, held, nb)

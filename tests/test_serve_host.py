@@ -114,3 +114,17 @@ def test_poisson_arrivals_and_request_recipe():
              if serve.make_request(i, i, n=4096, rows=16).kind == "inverse")
     zeroed = (r.row_gain == 0).mean(axis=1)
     assert np.all((zeroed >= 0.05) & (zeroed <= 0.35)) and r.x.shape == (3, 4096)
+
+
+def test_batch_charge_counts_the_long_fft_workspace():
+    """The HBM charge of a batch is the sum of the tensors it allocates, the
+    long-FFT workspace included (qtam_workspace_size of the batch), for every
+    batch size and both request kinds (host-only plan, no GPU)."""
+    from paper_2603_29785_gb300 import qtam
+    p = qtam.Plan(4096.0, 32768, (8.0,), 20.0, 2048.0, 128, device=-1)
+    for kind in ("forward", "inverse"):
+        for B in (1, 3, 8):
+            a = serve.batch_allocations(p, kind, B)
+            assert a["workspace"] == qtam.qtam_workspace_size(p.handle, B) > 0
+            assert a["y"] == B * p.info["envelope_bytes_per_segment"]
+            assert set(a) == ({"x", "y", "workspace"} | ({"gain", "xh"} if kind == "inverse" else set()))
