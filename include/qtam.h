@@ -88,7 +88,7 @@ enum { QTAM_WIN_BISQUARE = 0, QTAM_WIN_HANN = 1, QTAM_WIN_KAISER = 2, QTAM_WIN_T
  * NONE = 1. */
 enum { QTAM_NORM_L2 = 0, QTAM_NORM_PAPER = 1, QTAM_NORM_NONE = 2 };
 enum { QTAM_DTYPE_F32 = 0, QTAM_DTYPE_F64 = 1, QTAM_DTYPE_BF16 = 2, QTAM_DTYPE_F16 = 3 };
-enum { QTAM_SHORT_DFT_CUDA = 0, QTAM_SHORT_DFT_TENSOR = 1 };
+enum { QTAM_SHORT_DFT_CUDA = 0, QTAM_SHORT_DFT_TENSOR = 1, QTAM_SHORT_DFT_AUTO = 2 };
 
 typedef struct {
   double sample_rate;     /* f_s in Hz, > 0 */
@@ -122,7 +122,12 @@ typedef struct {
    * QTAM_ERR_UNSUPPORTED_SIZE).  The inverse runs the mirrored four-step
    * (DFT-128 then twiddle then DFT-64, on the tensor cores) when the
    * envelope pointer is 16-byte aligned, else the CUDA-core rows.  Both
-   * directions carry BF16 operand rounding (relative error ~3e-3). */
+   * directions carry BF16 operand rounding (relative error ~3e-3).
+   * QTAM_SHORT_DFT_AUTO picks the engine per plan: the tensor cores where
+   * their rounding is within the plan's own accuracy class (n_out = 8192,
+   * F32 compute, BF16 envelopes, no dense mode: there they are also the
+   * faster engine), the CUDA cores everywhere else; qtam_plan_info reports
+   * the choice. */
   int32_t short_dft;
   /* dense mode (the alternative inversion of Sec. III, beside the
    * demodulated default): stopband_eps > 0 gives every window the floor eps wherever it
@@ -312,7 +317,9 @@ QTAM_API qtam_status qtam_inverse_batched(const qtam_group* groups, int32_t n_gr
  * itself allocates nothing.  All calls on a device share that array: calls
  * whose kernels may overlap on the GPU (unordered streams) race and must be
  * serialised by the caller.  The first call on each device looks up the
- * array's address; make it before any stream capture. */
+ * array's address; make it before any stream capture.  A call with
+ * batch == 0 on a device plan returns QTAM_OK without that lookup and
+ * without launching anything. */
 QTAM_API qtam_status qtam_forward_noalloc(qtam_plan_t plan, const void* x, int64_t batch, void* y, void* stream);
 
 /* ---- Streaming analysis of a continuous signal (overlap-save) ----------

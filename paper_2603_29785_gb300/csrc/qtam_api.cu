@@ -759,7 +759,8 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   if (d->envelope_dtype < 0 || d->envelope_dtype > QTAM_DTYPE_F16) return fail(QTAM_ERR_INVALID_ARG, "unknown envelope dtype");
   if (d->max_window_hz < 0 || d->n_out < 0) return fail(QTAM_ERR_INVALID_ARG, "max_window_hz and n_out must be >= 0");
   if (d->length > ((int64_t)1 << 27)) return fail(QTAM_ERR_UNSUPPORTED_SIZE, "length above 2^27");
-  if (d->short_dft != QTAM_SHORT_DFT_CUDA && d->short_dft != QTAM_SHORT_DFT_TENSOR)
+  if (d->short_dft != QTAM_SHORT_DFT_CUDA && d->short_dft != QTAM_SHORT_DFT_TENSOR &&
+      d->short_dft != QTAM_SHORT_DFT_AUTO)
     return fail(QTAM_ERR_INVALID_ARG, "unknown short_dft");
   if (!std::isfinite(d->stopband_eps) || d->stopband_eps < 0 || (d->remodulate != 0 && d->remodulate != 1))
     return fail(QTAM_ERR_INVALID_ARG, "stopband_eps must be finite and >= 0, remodulate 0 or 1");
@@ -874,6 +875,13 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.threads = threads_for(pl->rc.rp, 0);
   pl->rc.smem = smem_for(pl->rc.rp, 0, pl->cplx_size());
   pl->rc.variant = -1;
+  if (pl->short_dft == QTAM_SHORT_DFT_AUTO) {
+    // the tensor cores where their BF16 rounding is inside the plan's accuracy
+    // class (BF16 envelopes) and they serve the length; CUDA cores otherwise
+    const bool tc_ok = tc_forward_supported(pl->M) && pl->compute == QTAM_DTYPE_F32 &&
+                       pl->env == QTAM_DTYPE_BF16 && pl->eps <= 0 && !pl->remod;
+    pl->short_dft = tc_ok ? QTAM_SHORT_DFT_TENSOR : QTAM_SHORT_DFT_CUDA;
+  }
   pl->rc.tensor = pl->short_dft == QTAM_SHORT_DFT_TENSOR && tc_forward_supported(pl->M);
   pl->rc.remod = pl->remod;
   pl->rc.dense = (pl->eps > 0 && pl->remod) ? 2 : (pl->eps > 0 || pl->remod) ? 1 : 0;

@@ -28,7 +28,7 @@ STATUS = {
 }
 NORM = {"l2": 0, "paper": 1, "none": 2}
 WINDOW = {"bisquare": 0, "hann": 1, "kaiser": 2, "tukey": 3, "planck": 4}
-SHORT_DFT = {"cuda": 0, "tensor": 1}
+SHORT_DFT = {"cuda": 0, "tensor": 1, "auto": 2}
 DTYPE = {"f32": 0, "f64": 1, "bf16": 2, "f16": 3}
 ENV_BYTES = {"f32": 8, "f64": 16, "bf16": 4, "f16": 4}
 

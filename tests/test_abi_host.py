@@ -176,6 +176,20 @@ def test_tensor_short_dft_options():
     assert _err(lambda: qtam.qtam_plan(d, -1)) == 1
 
 
+def test_short_dft_auto_picks_the_engine_per_plan():
+    """AUTO: tensor cores where their BF16 rounding is inside the plan's
+    accuracy class (M = 8192, F32 compute, BF16 envelopes, no dense mode),
+    CUDA cores otherwise; never an error where the CUDA cores serve."""
+    base = (4096.0, 32768, (8.0, 16.0), 20.0, 2048.0, 64)
+    auto = lambda **kw: qtam.Plan(*base, short_dft="auto", device=-1, **kw).info["short_dft"]
+    assert auto(n_out=8192, envelope="bf16") == 1
+    assert auto(n_out=8192) == 0                                # FP32 envelopes: FP32-accurate engine
+    assert auto(n_out=8192, envelope="f16") == 0                # FP16 storage is more accurate than BF16 operands
+    assert auto(envelope="bf16") == 0                           # M = 600: no tensor-core length
+    assert auto(n_out=8192, compute="f64", envelope="f64") == 0
+    assert auto(n_out=8192, envelope="bf16", remodulate=True) == 0
+
+
 def test_dense_mode_options():
     base = (4096.0, 8192, (8.0,), 20.0, 2048.0, 32)
     p = qtam.Plan(*base, stopband_eps=1e-6, p_floor_rel=0.0, device=-1)
