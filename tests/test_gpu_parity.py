@@ -76,7 +76,10 @@ SMALL = [
 
 
 # ---------------------------------------------------------------------------- stages
-@pytest.mark.parametrize("N", [256, 512, 3000, 4096, 6144, 16384, 24576, 262144, 524288])
+# powers of two from 2048 to 262144 samples run on thread-block clusters (one
+# per segment, 1 to 16 CTAs); the others on the three-pass kernels
+@pytest.mark.parametrize("N", [256, 512, 2048, 3000, 4096, 6144, 8192, 16384, 24576, 32768, 65536, 131072,
+                               262144, 524288])
 def test_spectrum_stage(N):
     p = make(4096.0, N, (8.0,), 30.0, 1000.0, 8, max_window_hz=20.0)
     B = 3

@@ -65,7 +65,7 @@ def test_every_variant_matches_oracle(M):
         assert rel(An[1], -Aref) < 1e-6, name
 
 
-@pytest.mark.parametrize("N", [4096, 65536, 524288])
+@pytest.mark.parametrize("N", [2048, 4096, 8192, 16384, 32768, 65536, 131072, 262144, 524288])
 def test_synthesis_stage_large(N):
     fs = 4096.0
     p = qtam.Plan(fs, N, (8.0,), 30.0, 1000.0, 16, max_window_hz=20.0, device=0)
