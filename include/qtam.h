@@ -397,10 +397,8 @@ QTAM_API qtam_status qtam_stream_destroy(qtam_stream_t s);
  * counted and reported by qtam_tc_status. */
 QTAM_API qtam_status qtam_tc_gemm_check(const void* A, const void* B, float* D, int32_t N, int32_t K, int32_t flags,
                                         void* stream);
-/* Number of bounded device waits that ran out since the library was loaded
- * on the current device: the tensor-core kernels' completion waits and the
- * bulk-staged inverse rows' copy waits (0 when every such kernel completed;
- * a row whose copy wait ran out is left out of the accumulation).
+/* Number of bounded tensor-core waits that ran out since the library was
+ * loaded on the current device (0 when every tensor-core kernel completed).
  * Synchronous. */
 QTAM_API qtam_status qtam_tc_status(int32_t* timeouts);
 

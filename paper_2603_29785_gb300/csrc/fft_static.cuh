@@ -150,19 +150,6 @@ template <int SIGN, int M, int NT, int NBS, int R0, int... Rs> struct StaticFFT 
     const size_t e = (size_t)M << NBS;
     return e + (e >> PS) + 1;
   }
-  // The input already sits in `sm` (e.g. staged there by a bulk copy, in
-  // the load functor's own layout): the first stage reads all of it into
-  // registers, waits for the whole block, then writes its outputs over it.
-  template <typename V, class Load, class Store>
-  __device__ __forceinline__ static void run_staged(V* sm, const V* tws, const Load& ld0, const Store& st0) {
-    static_assert(sizeof...(Rs) >= 1, "a staged input needs a shared-memory stage after the first");
-    const Strided<Load> ld{ld0};
-    const Strided<Store> st{st0};
-    SSmem<V, NBS, PS> io{sm};
-    sstage<SIGN, M, NT, NBS, 1, R0>(tws, ld, io, true);
-    __syncthreads();
-    SRun<SIGN, M, NT, NBS, PS, R0, Rs...>::run(sm, tws, st);
-  }
   template <typename V, class Load, class Store>
   __device__ __forceinline__ static void run(V* sm, const V* tws, const Load& ld0, const Store& st0) {
     const Strided<Load> ld{ld0};

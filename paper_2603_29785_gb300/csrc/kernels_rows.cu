@@ -18,92 +18,9 @@
 // The FFT itself is either the runtime engine (any 2^a 3^b 5^c length) or a
 // compile-time engine registered below for the lengths the workloads use.
 #include "rows_common.cuh"
-#include "tc_sm100.cuh"
 
 namespace qtam {
 namespace {
-
-// ---- inverse rows with the envelope row staged by one bulk copy ------------
-// One thread issues a single cp.async.bulk of the whole envelope row (M
-// values, contiguous, 16-byte multiple) into the FFT's own shared buffer,
-// completing on an mbarrier; the first stage then reads the row from shared
-// memory instead of issuing one global load per element.  The wait is
-// bounded: a copy that has not landed after ~1 s is counted in
-// g_bulk_timeouts (read with qtam_tc_status), the block gives it a second
-// bounded wait so its shared memory is not reused under it, and leaves.
-__device__ int g_bulk_timeouts = 0;
-
-template <typename V, int E> struct LoadStagedEnvelope {
-  const typename Env<V, E>::S* row;   // the envelope row in shared memory, natural order
-  __device__ __forceinline__ V get(int, int i) const { return Env<V, E>::from(row[i]); }
-};
-
-template <class Eng, int E>
-__global__ void __launch_bounds__(Eng::NT, Eng::MINB)
-    k_rows_inverse_bulk(const RowDev<float>* __restrict__ rows, const int* __restrict__ row_list, int n_sel,
-                        int n_rows, int64_t Nr, const typename Env<float2, E>::S* __restrict__ y,
-                        float2* __restrict__ A, const float2* __restrict__ twM) {
-  static_assert(Eng::NBS == 0, "one row per block");
-  using S = typename Env<float2, E>::S;
-  constexpr int M = Eng::M;
-  constexpr uint32_t kBytes = (uint32_t)(M * sizeof(S));
-  static_assert(kBytes % 16 == 0, "bulk copies move multiples of 16 bytes");
-  extern __shared__ __align__(16) unsigned char smraw[];
-  float2* sm = reinterpret_cast<float2*>(smraw);
-  __shared__ __align__(8) uint64_t bar;
-  const int64_t unit = blockIdx.x;   // the grid holds exactly one block per selected row
-  const int64_t seg = unit / n_sel;
-  const int row = row_list[unit - seg * n_sel];
-  if (threadIdx.x == 0) {
-    tc::mbar_init(&bar, 1);
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(tc::smem_addr(&bar)), "r"(kBytes)
-                 : "memory");
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(tc::smem_addr(sm)), "l"(y + (seg * n_rows + row) * M), "r"(kBytes), "r"(tc::smem_addr(&bar))
-                 : "memory");
-  }
-  const bool late = !tc::mbar_wait_bounded(&bar, 0, tc::kWaitCycles);
-  if (__syncthreads_or(late)) {
-    if (threadIdx.x == 0) {
-      atomicAdd(&g_bulk_timeouts, 1);
-      tc::mbar_wait_bounded(&bar, 0, tc::kWaitCycles);
-    }
-    __syncthreads();
-    return;
-  }
-  const LoadStagedEnvelope<float2, E> ld{reinterpret_cast<const S*>(sm)};
-  const AccumulateBand<float, true, Eng::PRED_RED> acc{A + seg * Nr,
-                                                       row_ctx<float, true>(rows, row, M, Nr, true, true, nullptr)};
-  Eng().template run_staged<-1>(sm, twM, ld, acc);
-}
-
-template <class Eng, int E>
-cudaError_t inv_launch_bulk(const RowDev<float>* rows, const int* row_list, int n_sel, int n_rows, int64_t Nr,
-                            const void* y, float2* A, int64_t B, const float2* twM, cudaStream_t st) {
-  // the bulk copy needs a 16-byte aligned source row: other pointers take the
-  // per-element loads of the same variant
-  if (reinterpret_cast<uintptr_t>(y) & 15u) return inv_launch<Eng, E>(rows, row_list, n_sel, n_rows, Nr, y, A, B, twM, st);
-  const int64_t units = B * n_sel;
-  if (units == 0) return cudaSuccess;
-  const size_t smem = Eng::smem_bytes(sizeof(float2));
-  allow_smem((const void*)k_rows_inverse_bulk<Eng, E>, smem);
-  k_rows_inverse_bulk<Eng, E><<<(unsigned)units, Eng::NT, smem, st>>>(
-      rows, row_list, n_sel, n_rows, Nr, static_cast<const typename Env<float2, E>::S*>(y), A, twM);
-  return cudaGetLastError();
-}
-
-// the variant with the bulk-staged inverse (FP32, BF16 and FP16 envelopes)
-template <class Eng> RowVariant make_variant_bulk(const char* name) {
-  RowVariant v = make_variant<Eng>(name);
-  v.inv[ENV_F32] = inv_launch_bulk<Eng, ENV_F32>;
-  v.inv[ENV_BF16] = inv_launch_bulk<Eng, ENV_BF16>;
-  v.inv[ENV_F16] = inv_launch_bulk<Eng, ENV_F16>;
-  return v;
-}
 
 // StaticEngine<M, log2 rows per block, min blocks per SM, radices...>; the
 // first variant listed for a length is the default before tuning.
@@ -113,9 +30,6 @@ template <class Eng> RowVariant make_variant_bulk(const char* name) {
   make_variant<StaticEngine<M, NBS, MINB, __VA_ARGS__>>(#M ":" #__VA_ARGS__ " rows/blk 2^" #NBS " minblk " #MINB)
 #define QTAM_VT(M, NBS, MINB, ...) \
   make_variant_tab<StaticEngine<M, NBS, MINB, __VA_ARGS__>>(#M ":" #__VA_ARGS__ " rows/blk 2^" #NBS " minblk " #MINB)
-#define QTAM_VB(M, NBS, MINB, ...)                                                                       \
-  make_variant_bulk<StaticEngine<M, NBS, MINB, __VA_ARGS__>>(#M ":" #__VA_ARGS__ " rows/blk 2^" #NBS " minblk " #MINB \
-                                                             " bulk-staged inverse")
 const RowVariant kVariants[] = {
     QTAM_VT(4800, 0, 4, 16, 20, 15),
     QTAM_V(4800, 0, 3, 16, 20, 15),
@@ -138,11 +52,9 @@ const RowVariant kVariants[] = {
     QTAM_VT(8192, 0, 1, 16, 16, 32),
     QTAM_V(8192, 0, 1, 32, 16, 16),
     QTAM_V(8192, 0, 1, 16, 32, 16),
-    QTAM_VB(4800, 0, 4, 16, 20, 15),
 };
 #undef QTAM_V
 #undef QTAM_VT
-#undef QTAM_VB
 
 template <typename V, int E>
 __global__ void k_scale_rows(typename Env<V, E>::S* __restrict__ y, const float* __restrict__ gain, int64_t n_rows,
@@ -258,16 +170,6 @@ cudaError_t launch_scale_rows(void* y, int env, const float* gain, int64_t n_row
     default: k_scale_rows<float2, ENV_F32><<<blocks, 256, 0, st>>>(static_cast<float2*>(y), gain, n_rows, M);
   }
   return cudaGetLastError();
-}
-
-// bounded bulk-copy waits of the inverse rows that ran out (qtam_tc_status)
-int rows_bulk_timeouts() {
-  int v = 0;
-  if (cudaMemcpyFromSymbol(&v, g_bulk_timeouts, sizeof(int)) != cudaSuccess) {
-    cudaGetLastError();
-    return 0;
-  }
-  return v;
 }
 
 // the dense-mode variants follow the ones registered here

@@ -897,7 +897,7 @@ qtam_status qtam_tc_status(int32_t* timeouts) {
     qtam::set_last_error(std::string("tc status: ") + cudaGetErrorString(e));
     return QTAM_ERR_CUDA;
   }
-  *timeouts = v + qtam::rows_bulk_timeouts();
+  *timeouts = v;
   return QTAM_OK;
 }
 

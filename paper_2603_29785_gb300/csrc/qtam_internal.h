@@ -160,8 +160,6 @@ qtam_status stream_inverse_fused(qtam_plan_s* pl, const void* hist, int hcols, c
                                  cudaStream_t st, bool* used);
 
 int row_variant_count();
-// bounded bulk-copy waits of the bulk-staged inverse rows that ran out
-int rows_bulk_timeouts();
 // per (segment, plane) pair: energy = sum |Y|^2 (FP64), peak = max |Y|^2 over K*M values
 cudaError_t launch_plane_metrics(const void* y, int env, int64_t pairs, int64_t per_plane, double* energy, float* peak,
                                  cudaStream_t st);

@@ -254,10 +254,6 @@ template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
   __device__ __forceinline__ void run(V* sm, const V* tws, const L& ld, const St& st) const {
     StaticFFT<S, M, NT, NBS, Rs...>::run(sm, tws, ld, st);
   }
-  template <int S, typename V, class L, class St>
-  __device__ __forceinline__ void run_staged(V* sm, const V* tws, const L& ld, const St& st) const {
-    StaticFFT<S, M, NT, NBS, Rs...>::run_staged(sm, tws, ld, st);
-  }
   static size_t smem_bytes(size_t elem) { return StaticFFT<1, M, NT, NBS, Rs...>::smem_elems() * elem; }
 };
 
