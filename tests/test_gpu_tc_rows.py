@@ -132,3 +132,25 @@ def test_tensor_inverse_envelope_dtypes_and_unaligned_pointer():
     y_off.copy_(torch.from_numpy(Y.astype(np.complex64)))
     A = p.accumulate(y_off).cpu().numpy().astype(np.complex128)[0]
     assert _rel(A, ref) < 1e-5
+
+
+def test_short_dft_auto_engine_and_accuracy():
+    """short_dft = AUTO takes the tensor cores for an M = 8192 plan with BF16
+    envelopes (their rounding is inside that plan's accuracy class: bound
+    1e-2 against the oracle) and the CUDA cores for FP32 envelopes (FP32
+    bound 1e-6), forward and round trip."""
+    fs, N, qs, K = 4096.0, 32768, (8.0, 16.0), 64
+    g = O.geometry(fs, N, qs, 20.0, 2048.0, K, n_out=8192)
+    x = np.stack([synth.glitchy_segment(70 + b, N, fs, chirp=True) for b in range(2)])
+    xd = torch.from_numpy(x).cuda()
+    refs = [O.forward(g, x[b].astype(np.float64)) for b in range(2)]
+    for env, engine, bound, rt in (("bf16", 1, 1e-2, 2e-2), ("f32", 0, 1e-6, 1e-5)):
+        p = qtam.Plan(fs, N, qs, 20.0, 2048.0, K, n_out=8192, short_dft="auto", envelope=env, device=0)
+        assert p.info["short_dft"] == engine, env
+        y = p.forward(xd)
+        Y = _np(y)
+        for b in range(2):
+            assert _rel(Y[b], refs[b]) < bound, env
+        xh = p.inverse(y).cpu().numpy().astype(np.float64)
+        for b in range(2):
+            assert _rel(xh[b], O.projection(g, x[b].astype(np.float64), tau=p.info["p_floor_rel"])) < rt, env
