@@ -289,6 +289,7 @@ template <int S> struct Dft<15, S> : DftPFA<3, 5, S> {};
 template <int S> struct Dft<16, S> : DftComposite<4, 4, S> {};
 template <int S> struct Dft<18, S> : DftPFA<2, 9, S> {};
 template <int S> struct Dft<20, S> : DftPFA<4, 5, S> {};
+template <int S> struct Dft<24, S> : DftPFA<8, 3, S> {};
 template <int S> struct Dft<25, S> : DftComposite<5, 5, S> {};
 template <int S> struct Dft<27, S> : DftComposite<3, 9, S> {};
 template <int S> struct Dft<32, S> : DftComposite<4, 8, S> {};

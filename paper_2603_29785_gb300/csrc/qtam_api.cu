@@ -886,11 +886,14 @@ qtam_status qtam_plan(const qtam_plan_desc* d, int device, qtam_plan_t* out) {
   pl->rc.remod = pl->remod;
   pl->rc.dense = (pl->eps > 0 && pl->remod) ? 2 : (pl->eps > 0 || pl->remod) ? 1 : 0;
   if (!dbl) {
-    for (int v = 0; v < row_variant_count(); ++v)
-      if (variant_usable(pl, v)) {
-        pl->rc.variant = v;   // first registered usable variant for this length
-        break;
-      }
+    // the first usable variant marked preferred for this length, else the
+    // first registered usable one
+    for (int pass = 0; pass < 2 && pl->rc.variant < 0; ++pass)
+      for (int v = 0; v < row_variant_count(); ++v)
+        if (variant_usable(pl, v) && (pass == 1 || row_variant(v)->preferred)) {
+          pl->rc.variant = v;
+          break;
+        }
   }
   if (pl->rc.threads > kMaxThreads || pl->rc.smem > (size_t)kMaxSmem) {
     free_plan(pl);

@@ -126,6 +126,7 @@ struct RowVariant {
   RowFwdDenseFn fwd_dense;   // null unless built for the dense mode
   RowInvDenseFn inv_dense;
   int tw_pair = 0;   // stage tables in the row-pair format (c, c, s, s) per entry (kernels_rows_pair.cu)
+  int preferred = 0;   // default of its length for bisquare plans ahead of the other variants
 };
 // the dense-mode variants live in their own translation unit (kernels_rows_dense.cu)
 int dense_row_variant_count();
@@ -133,6 +134,9 @@ const RowVariant* dense_row_variant(int i);
 // the row-pair variants (packed FP32x2, two rows per block) in kernels_rows_pair.cu
 int pair_row_variant_count();
 const RowVariant* pair_row_variant(int i);
+// balanced-radix variants for the short envelope lengths (kernels_rows_short.cu)
+int short_row_variant_count();
+const RowVariant* short_row_variant(int i);
 // Fused streaming row kernels (kernels_rows_stream.cu) of a compile-time
 // variant, looked up by the variant's name: forward with the crop-and-phase
 // store into the map, inverse with the history/new-columns chunk load.

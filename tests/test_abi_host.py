@@ -249,3 +249,19 @@ def test_batched_workspace_is_largest_group():
         qtam.qtam_forward_batched([ga, gb], 0, want, stream=0)   # host-only plans cannot run
     with pytest.raises(qtam.QtamError):
         qtam.qtam_batched_workspace_size([(a.handle, 0, 0, -1)])
+
+
+def test_short_length_defaults_are_the_balanced_variants():
+    """Bisquare plans at M = 1200, 600, 300, 150 start on their preferred
+    balanced-radix variant; a window-table plan of the same length keeps the
+    first table-capable variant; M = 4800 keeps its first registered one."""
+    want = {16: "1200:10, 12, 10 rows/blk 2^0 minblk 8", 8: "600:25, 24 rows/blk 2^2 minblk 4",
+            4: "300:15, 20 rows/blk 2^2 minblk 4", 2: "150:10, 15 rows/blk 2^4 minblk 2"}
+    for dur, name in want.items():
+        p = qtam.Plan(4096.0, 4096 * dur, (8.0, 16.0, 32.0), 20.0, 2048.0, 128, device=-1)
+        assert qtam.qtam_variant_describe(p.info["row_variant"])["name"] == name
+        assert p.info["row_variant"] in qtam.qtam_plan_variants(p.handle)
+        h = qtam.Plan(4096.0, 4096 * dur, (8.0, 16.0, 32.0), 20.0, 2048.0, 128, window="hann", device=-1)
+        assert h.info["row_variant"] == qtam.qtam_plan_variants(h.handle)[1]
+    b = qtam.Plan(4096.0, 262144, (4, 8, 16, 32, 64), 20.0, 2048.0, 128, device=-1)
+    assert qtam.qtam_variant_describe(b.info["row_variant"])["name"] == "4800:16, 20, 15 rows/blk 2^0 minblk 4"
