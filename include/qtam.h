@@ -254,10 +254,13 @@ QTAM_API qtam_status qtam_inverse_single_tile(qtam_plan_t plan, const void* y, i
  * split into inner chunks of about 16 MB of input and short first and last
  * chunks (about batch/16 segments; at most 10 chunks): host-to-device
  * copies run on one library-owned stream and device-to-host copies on
- * another, ordered against the transforms on `stream` by events, so the
- * copies of neighbouring chunks overlap the transforms (pinned host buffers
- * make the copies asynchronous).  One round trip at a time per plan (calls
- * on the same plan serialise).  All device buffers are caller-owned
+ * another, ordered against the transforms by events, so the copies of
+ * neighbouring chunks overlap the transforms (pinned host buffers make the
+ * copies asynchronous).  Even chunks are transformed on `stream`; when the
+ * workspace holds two workspaces of the largest chunk (and is 256-byte
+ * aligned), odd chunks run on a third library-owned stream in the second
+ * one, so neighbouring chunks' kernels overlap.  One round trip at a time
+ * per plan (calls on the same plan serialise).  All device buffers are caller-owned
  * ([batch][N], [batch][P][K][M], [batch][N]); workspace as for qtam_forward
  * with `batch` segments. */
 QTAM_API qtam_status qtam_roundtrip_host(qtam_plan_t plan, const void* x_host, int64_t batch, uint64_t plane_mask,

@@ -211,7 +211,7 @@ struct qtam_plan_s {
   // host round trip pipeline: copy-in and copy-out streams and their events,
   // created on first use; one round trip at a time per plan (rt_mu)
   std::mutex rt_mu;
-  cudaStream_t rt_in = nullptr, rt_out = nullptr;
+  cudaStream_t rt_in = nullptr, rt_out = nullptr, rt_cs = nullptr;
   std::vector<cudaEvent_t> rt_ev;
 
   size_t real_size() const { return compute == QTAM_DTYPE_F64 ? 8 : 4; }
@@ -554,6 +554,7 @@ void free_plan(qtam_plan_s* pl) {
     for (cudaEvent_t e : pl->rt_ev) cudaEventDestroy(e);
     if (pl->rt_in) cudaStreamDestroy(pl->rt_in);
     if (pl->rt_out) cudaStreamDestroy(pl->rt_out);
+    if (pl->rt_cs) cudaStreamDestroy(pl->rt_cs);
     for (auto& kv : pl->masks) {
       cudaFree(kv.second.invP);
       cudaFree(kv.second.rows);
@@ -1190,6 +1191,7 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
   if (!pl->rt_in) {
     e = cudaStreamCreateWithFlags(&pl->rt_in, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->rt_out, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&pl->rt_cs, cudaStreamNonBlocking);
     for (int i = 0; i < 2 * kChunks + 2 && e == cudaSuccess; ++i) {
       cudaEvent_t ev;
       e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
@@ -1198,7 +1200,7 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
     if (e != cudaSuccess) return fail_cuda(e, "round-trip streams");
   }
   // chunk c holds segments [bound[c], bound[c + 1]); copies of neighbouring
-  // chunks overlap the transforms of chunk c on the caller's stream.  Inner
+  // chunks overlap the transforms of chunk c.  Inner
   // chunks carry about 16 MB of input (smaller ones pay per-chunk launch and
   // tail costs; measured best on the 64 s workload); the first and last
   // chunks are cut to about B/16 segments, since their copies cannot overlap
@@ -1221,13 +1223,25 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
   }
   const int C = (int)bound.size() - 1;
   const size_t ys = (size_t)pl->P * pl->K * pl->M * pl->env_size();
+  // Odd chunks run on a second library-owned stream with their own half of
+  // the workspace when two chunk workspaces fit, so a chunk's first kernels
+  // fill the last waves of the one before (short chunks leave the GPU half
+  // idle in their tails); even chunks stay on the caller's stream.
+  int64_t maxnb = 0;
+  for (int c = 0; c < C; ++c) maxnb = std::max<int64_t>(maxnb, bound[c + 1] - bound[c]);
+  const size_t slot = (ws_bytes(pl, maxnb) + 255) / 256 * 256;
+  const bool two = C > 1 && 2 * slot <= wsb && (reinterpret_cast<uintptr_t>(ws) & 255u) == 0;
+  auto chunk_stream = [&](int c) { return (two && (c & 1)) ? pl->rt_cs : st; };
+  auto chunk_ws = [&](int c) { return (two && (c & 1)) ? static_cast<void*>(static_cast<char*>(ws) + slot) : ws; };
+  const size_t chunk_wsb = two ? slot : wsb;
   cudaEvent_t ev_start = pl->rt_ev[0], ev_end = pl->rt_ev[1];
   cudaEvent_t* ev_in = &pl->rt_ev[2];
   cudaEvent_t* ev_done = &pl->rt_ev[2 + kChunks];
   auto seg0 = [&](int c) { return bound[c]; };
   if ((e = cudaEventRecord(ev_start, st)) != cudaSuccess) return fail_cuda(e, "cudaEventRecord");
   if ((e = cudaStreamWaitEvent(pl->rt_in, ev_start, 0)) != cudaSuccess ||
-      (e = cudaStreamWaitEvent(pl->rt_out, ev_start, 0)) != cudaSuccess)
+      (e = cudaStreamWaitEvent(pl->rt_out, ev_start, 0)) != cudaSuccess ||
+      (two && (e = cudaStreamWaitEvent(pl->rt_cs, ev_start, 0)) != cudaSuccess))
     return fail_cuda(e, "cudaStreamWaitEvent");
   for (int c = 0; c < C; ++c) {
     const int64_t s0 = seg0(c), nb = seg0(c + 1) - s0;
@@ -1238,13 +1252,14 @@ qtam_status qtam_roundtrip_host(qtam_plan_t pl, const void* x_host, int64_t B, u
   }
   for (int c = 0; c < C; ++c) {
     const int64_t s0 = seg0(c), nb = seg0(c + 1) - s0;
-    if ((e = cudaStreamWaitEvent(st, ev_in[c], 0)) != cudaSuccess) return fail_cuda(e, "cudaStreamWaitEvent");
+    cudaStream_t cs = chunk_stream(c);
+    if ((e = cudaStreamWaitEvent(cs, ev_in[c], 0)) != cudaSuccess) return fail_cuda(e, "cudaStreamWaitEvent");
     void* xc = static_cast<char*>(x_dev) + s0 * xs;
     void* yc = static_cast<char*>(y_dev) + s0 * ys;
     void* hc = static_cast<char*>(xhat_dev) + s0 * xs;
-    if ((s = qtam_forward(pl, xc, nb, yc, ws, wsb, stream)) != QTAM_OK) return s;
-    if ((s = qtam_inverse(pl, yc, nb, mask, hc, ws, wsb, stream)) != QTAM_OK) return s;
-    if ((e = cudaEventRecord(ev_done[c], st)) != cudaSuccess ||
+    if ((s = qtam_forward(pl, xc, nb, yc, chunk_ws(c), chunk_wsb, cs)) != QTAM_OK) return s;
+    if ((s = qtam_inverse(pl, yc, nb, mask, hc, chunk_ws(c), chunk_wsb, cs)) != QTAM_OK) return s;
+    if ((e = cudaEventRecord(ev_done[c], cs)) != cudaSuccess ||
         (e = cudaStreamWaitEvent(pl->rt_out, ev_done[c], 0)) != cudaSuccess)
       return fail_cuda(e, "chunk ordering");
     e = cudaMemcpyAsync(static_cast<char*>(xhat_host) + s0 * xs, hc, nb * xs, cudaMemcpyDeviceToHost, pl->rt_out);
