@@ -20,7 +20,7 @@ BUILDDIR = os.path.join(LIBDIR, "_build")
 LIBNAME = "libqtam.so"
 SOURCES = ["qtam_api.cu", "kernels_long.cu", "kernels_rows.cu", "qtam_noalloc.cu", "qtam_stream.cu",
            "kernels_tc.cu", "kernels_rows_stream.cu", "kernels_rows_dense.cu", "kernels_rows_pair.cu",
-           "kernels_rows_short.cu"]
+           "kernels_rows_tuned.cu"]
 HEADERS = ["fft_core.cuh", "fft_static.cuh", "qtam_internal.h", "tc_sm100.cuh", "rows_common.cuh", "pair_fft.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden",

@@ -176,7 +176,7 @@ cudaError_t launch_scale_rows(void* y, int env, const float* gain, int64_t n_row
 // and the row-pair variants follow those
 constexpr int kMainVariants = (int)(sizeof(kVariants) / sizeof(kVariants[0]));
 int row_variant_count() {
-  return kMainVariants + dense_row_variant_count() + pair_row_variant_count() + short_row_variant_count();
+  return kMainVariants + dense_row_variant_count() + pair_row_variant_count() + tuned_row_variant_count();
 }
 const RowVariant* row_variant(int i) {
   if (i < 0) return nullptr;
@@ -185,7 +185,7 @@ const RowVariant* row_variant(int i) {
   if (i < dense_row_variant_count()) return dense_row_variant(i);
   i -= dense_row_variant_count();
   if (i < pair_row_variant_count()) return pair_row_variant(i);
-  return short_row_variant(i - pair_row_variant_count());
+  return tuned_row_variant(i - pair_row_variant_count());
 }
 
 template <typename T>

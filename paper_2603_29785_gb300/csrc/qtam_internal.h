@@ -134,9 +134,10 @@ const RowVariant* dense_row_variant(int i);
 // the row-pair variants (packed FP32x2, two rows per block) in kernels_rows_pair.cu
 int pair_row_variant_count();
 const RowVariant* pair_row_variant(int i);
-// balanced-radix variants for the short envelope lengths (kernels_rows_short.cu)
-int short_row_variant_count();
-const RowVariant* short_row_variant(int i);
+// variants added after measurement (kernels_rows_tuned.cu): balanced radices for
+// the short lengths, a four-stage sequence at M = 8192
+int tuned_row_variant_count();
+const RowVariant* tuned_row_variant(int i);
 // Fused streaming row kernels (kernels_rows_stream.cu) of a compile-time
 // variant, looked up by the variant's name: forward with the crop-and-phase
 // store into the map, inverse with the history/new-columns chunk load.

@@ -167,7 +167,9 @@ def test_tensor_short_dft_options():
     base = (4096.0, 32768, (8.0, 16.0), 20.0, 2048.0, 64)
     p = qtam.Plan(*base, n_out=8192, short_dft="tensor", device=-1)
     assert p.info["short_dft"] == 1 and p.M == 8192
-    assert len(qtam.qtam_plan_variants(p.handle)) == 4      # runtime engine + 3 compile-time inverse variants
+    vs = qtam.qtam_plan_variants(p.handle)                 # runtime engine + the compile-time inverse variants
+    assert vs[0] == -1 and len(vs) >= 4
+    assert all(qtam.qtam_variant_describe(v)["name"].startswith("8192:") for v in vs[1:])
     assert qtam.Plan(*base, device=-1).info["short_dft"] == 0
     assert _err(lambda: qtam.Plan(*base, short_dft="tensor", device=-1)) == 2                    # M = 600
     assert _err(lambda: qtam.Plan(*base, n_out=8192, short_dft="tensor", compute="f64", device=-1)) == 2
@@ -251,10 +253,11 @@ def test_batched_workspace_is_largest_group():
         qtam.qtam_batched_workspace_size([(a.handle, 0, 0, -1)])
 
 
-def test_short_length_defaults_are_the_balanced_variants():
+def test_tuned_defaults_per_length():
     """Bisquare plans at M = 1200, 600, 300, 150 start on their preferred
-    balanced-radix variant; a window-table plan of the same length keeps the
-    first table-capable variant; M = 4800 keeps its first registered one."""
+    balanced-radix variant and M = 8192 on its four-stage one; a window-table
+    plan of the same length keeps the first table-capable variant; M = 4800
+    keeps its first registered one."""
     want = {16: "1200:10, 12, 10 rows/blk 2^0 minblk 8", 8: "600:25, 24 rows/blk 2^2 minblk 4",
             4: "300:15, 20 rows/blk 2^2 minblk 4", 2: "150:10, 15 rows/blk 2^4 minblk 2"}
     for dur, name in want.items():
@@ -265,3 +268,6 @@ def test_short_length_defaults_are_the_balanced_variants():
         assert h.info["row_variant"] == qtam.qtam_plan_variants(h.handle)[1]
     b = qtam.Plan(4096.0, 262144, (4, 8, 16, 32, 64), 20.0, 2048.0, 128, device=-1)
     assert qtam.qtam_variant_describe(b.info["row_variant"])["name"] == "4800:16, 20, 15 rows/blk 2^0 minblk 4"
+    # M = 8192 on CUDA cores: the four-stage sequence at two blocks per SM
+    e = qtam.Plan(4096.0, 262144, (4, 8, 16, 32, 64), 20.0, 2048.0, 128, n_out=8192, device=-1)
+    assert qtam.qtam_variant_describe(e.info["row_variant"])["name"] == "8192:16, 8, 8, 8 rows/blk 2^0 minblk 2"
