@@ -168,6 +168,24 @@ def test_stream_fused_row_kernels_m600():
     assert _rel(xm, O.stream_inverse(g, Yg, hop, planes=[1], tau=tau)) < 1e-5
 
 
+def test_stream_fused_row_kernels_m8192_cuda_cores():
+    """M = 8192 on CUDA cores: the four-stage default variant's fused
+    streaming kernels against the oracle's stream at FP32 accuracy."""
+    cfg = dict(fs=4096.0, N=32768, qs=(8.0, 16.0), fmin=20.0, fmax=2048.0, K=32, n_out=8192)
+    p, g = _plan(cfg, short_dft="cuda")
+    assert p.M == 8192
+    assert qtam.qtam_variant_describe(p.info["row_variant"])["name"] == "8192:16, 8, 8, 8 rows/blk 2^0 minblk 2"
+    hop = 16384
+    s = qtam.Stream(p, hop=hop, max_chunks=4)
+    x = synth.glitchy_segment(23, 6 * hop, 4096.0, chirp=True).astype(np.float32)
+    Y = _push(s, torch.from_numpy(x).cuda(), [2, 1, 3])
+    Yg = _np(Y)
+    Yo = O.stream_forward(g, x.astype(np.float64), hop)
+    assert _rel(Yg, Yo) < 1e-6
+    xh = _np(s.inverse(Y.contiguous()))
+    assert _rel(xh, O.stream_inverse(g, Yg, hop, tau=p.info["p_floor_rel"])) < 1e-5
+
+
 def test_stream_over_tensor_core_plan():
     """A stream over a plan with the tensor-core short DFT (M = 8192, both
     directions on tcgen05) against the oracle's stream, at the BF16 bound of
