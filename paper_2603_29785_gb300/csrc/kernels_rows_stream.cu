@@ -120,6 +120,12 @@ cudaError_t inv_chunk_launch(const RowDev<float>* rows, const int* row_list, int
         fwd_crop_launch<StaticEngine<M, NBS, MINB, __VA_ARGS__>>,                                       \
         inv_chunk_launch<StaticEngine<M, NBS, MINB, __VA_ARGS__>>                                        \
   }
+#define QTAM_VS_NT(NT, M, NBS, MINB, ...)                                                                 \
+  StreamRowFns {                                                                                          \
+    #M ":" #__VA_ARGS__ " rows/blk 2^" #NBS " minblk " #MINB " threads " #NT,                              \
+        fwd_crop_launch<ThreadsEngine<NT, M, NBS, MINB, __VA_ARGS__>>,                                     \
+        inv_chunk_launch<ThreadsEngine<NT, M, NBS, MINB, __VA_ARGS__>>                                     \
+  }
 const StreamRowFns kStreamFns[] = {
     QTAM_VS(4800, 0, 4, 16, 20, 15), QTAM_VS(2400, 0, 3, 16, 10, 15), QTAM_VS(1200, 1, 2, 16, 15, 5),
     QTAM_VS(600, 3, 2, 8, 3, 25),    QTAM_VS(500, 3, 2, 4, 5, 25),    QTAM_VS(300, 3, 2, 12, 25),
@@ -127,8 +133,10 @@ const StreamRowFns kStreamFns[] = {
     // the preferred defaults of kernels_rows_tuned.cu
     QTAM_VS(1200, 0, 8, 10, 12, 10), QTAM_VS(600, 2, 4, 25, 24),      QTAM_VS(300, 2, 4, 15, 20),
     QTAM_VS(150, 4, 2, 10, 15),      QTAM_VS(8192, 0, 2, 16, 8, 8, 8),
+    QTAM_VS_NT(160, 2400, 0, 6, 16, 10, 15),
 };
 #undef QTAM_VS
+#undef QTAM_VS_NT
 
 }  // namespace
 

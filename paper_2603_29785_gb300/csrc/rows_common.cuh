@@ -257,6 +257,19 @@ template <int M_, int NBS_, int MINB_, int... Rs> struct StaticEngine {
   static size_t smem_bytes(size_t elem) { return StaticFFT<1, M, NT, NBS, Rs...>::smem_elems() * elem; }
 };
 
+// The same engine with an explicit block size NT_: a stage with more
+// butterfly items than threads runs in rounds, so the block can be sized to
+// the stages' common item count instead of the widest stage's (at M = 2400,
+// 16·10·15 has 150 / 240 / 160 items: 160 threads run the 10-point stage in
+// two rounds and the others in one).
+template <int NT_, int M_, int NBS_, int MINB_, int... Rs> struct ThreadsEngine : StaticEngine<M_, NBS_, MINB_, Rs...> {
+  static constexpr int NT = NT_;
+  template <int S, typename V, class L, class St>
+  __device__ __forceinline__ void run(V* sm, const V* tws, const L& ld, const St& st) const {
+    StaticFFT<S, M_, NT_, NBS_, Rs...>::run(sm, tws, ld, st);
+  }
+};
+
 template <typename T, bool FEXACT>
 __device__ __forceinline__ RowCtx<T, FEXACT> row_ctx(const RowDev<T>* rows, int row, int M, int64_t Nr, bool valid,
                                                      bool inv, const T* wtab) {

@@ -255,10 +255,12 @@ def test_batched_workspace_is_largest_group():
 
 def test_tuned_defaults_per_length():
     """Bisquare plans at M = 1200, 600, 300, 150 start on their preferred
-    balanced-radix variant and M = 8192 on its four-stage one; a window-table
+    balanced-radix variant, M = 2400 on its 160-thread one and M = 8192 on
+    its four-stage one; a window-table
     plan of the same length keeps the first table-capable variant; M = 4800
     keeps its first registered one."""
-    want = {16: "1200:10, 12, 10 rows/blk 2^0 minblk 8", 8: "600:25, 24 rows/blk 2^2 minblk 4",
+    want = {32: "2400:16, 10, 15 rows/blk 2^0 minblk 6 threads 160",
+            16: "1200:10, 12, 10 rows/blk 2^0 minblk 8", 8: "600:25, 24 rows/blk 2^2 minblk 4",
             4: "300:15, 20 rows/blk 2^2 minblk 4", 2: "150:10, 15 rows/blk 2^4 minblk 2"}
     for dur, name in want.items():
         p = qtam.Plan(4096.0, 4096 * dur, (8.0, 16.0, 32.0), 20.0, 2048.0, 128, device=-1)

@@ -186,6 +186,24 @@ def test_stream_fused_row_kernels_m8192_cuda_cores():
     assert _rel(xh, O.stream_inverse(g, Yg, hop, tau=p.info["p_floor_rel"])) < 1e-5
 
 
+def test_stream_fused_row_kernels_m2400_threads_160():
+    """32 s chunks at 4096 Hz (M = 2400): the 160-thread default variant's
+    fused streaming kernels against the oracle's stream at FP32 accuracy."""
+    cfg = dict(fs=4096.0, N=131072, qs=(8.0, 16.0, 32.0), fmin=20.0, fmax=2048.0, K=128)
+    p, g = _plan(cfg)
+    assert p.M == 2400
+    assert qtam.qtam_variant_describe(p.info["row_variant"])["name"] == "2400:16, 10, 15 rows/blk 2^0 minblk 6 threads 160"
+    hop = 65536
+    s = qtam.Stream(p, hop=hop, max_chunks=3)
+    x = synth.glitchy_segment(29, 5 * hop, 4096.0, chirp=True).astype(np.float32)
+    Y = _push(s, torch.from_numpy(x).cuda(), [2, 1, 2])
+    Yg = _np(Y)
+    Yo = O.stream_forward(g, x.astype(np.float64), hop)
+    assert _rel(Yg, Yo) < 1e-6
+    xh = _np(s.inverse(Y.contiguous()))
+    assert _rel(xh, O.stream_inverse(g, Yg, hop, tau=p.info["p_floor_rel"])) < 1e-5
+
+
 def test_stream_over_tensor_core_plan():
     """A stream over a plan with the tensor-core short DFT (M = 8192, both
     directions on tcgen05) against the oracle's stream, at the BF16 bound of
