@@ -131,8 +131,8 @@ const StreamRowFns kStreamFns[] = {
     QTAM_VS(600, 3, 2, 8, 3, 25),    QTAM_VS(500, 3, 2, 4, 5, 25),    QTAM_VS(300, 3, 2, 12, 25),
     QTAM_VS(150, 4, 2, 6, 25),       QTAM_VS(75, 5, 2, 3, 25),        QTAM_VS(8192, 0, 1, 16, 16, 32),
     // the preferred defaults of kernels_rows_tuned.cu
-    QTAM_VS(1200, 0, 8, 10, 12, 10), QTAM_VS(600, 2, 4, 25, 24),      QTAM_VS(300, 2, 4, 15, 20),
-    QTAM_VS(150, 4, 2, 10, 15),      QTAM_VS(8192, 0, 2, 16, 8, 8, 8),
+    QTAM_VS(1200, 0, 8, 10, 12, 10), QTAM_VS(600, 1, 8, 25, 24),      QTAM_VS(300, 1, 12, 15, 20),
+    QTAM_VS(150, 3, 4, 10, 15),      QTAM_VS(8192, 0, 2, 16, 8, 8, 8),
     QTAM_VS_NT(160, 2400, 0, 6, 16, 10, 15),
 };
 #undef QTAM_VS

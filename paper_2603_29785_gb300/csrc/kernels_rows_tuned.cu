@@ -19,9 +19,12 @@ namespace {
 
 // Measured per length against the older shapes (forward + inverse of one
 // launch over 38-48 segments at 4096 Hz, Q {8,16,32} x 128 rows): M = 1200
-// 0.142 against 0.200 ms, M = 600 0.087 against 0.121 ms, M = 300 0.051
-// against 0.066 ms, M = 150 0.051 against 0.053 ms; at M = 75 the two shapes
-// trade places with the sample rate, so the older one stays the default.  At
+// 0.142 against 0.200 ms, M = 600 0.081 against 0.121 ms (2 rows per
+// 64-thread block; 0.087 at 4 rows per block), M = 300 0.054 against 0.066
+// ms (2 rows per block, 12 blocks per SM), M = 150 0.049 against 0.053 ms;
+// at M = 75 the two shapes trade places with the sample rate, so the older
+// one stays the default.  Fewer rows per block with more blocks per SM won
+// at every short length: a block's barrier then waits on fewer threads.  At
 // M = 8192 (64 s segments, Q {4..64} x 128 rows, 64 segments, FP32
 // envelopes) 16·8·8·8 at 2 blocks per SM takes 1.010 + 0.889 ms against
 // 1.215 + 1.315 ms for 16·16·32 at one block.  At M = 2400 (32 s segments,
@@ -47,12 +50,14 @@ template <class Eng> RowVariant make_variant_pref(const char* name) {
 const RowVariant kTunedVariants[] = {
     QTAM_VS(1200, 0, 8, 10, 12, 10),
     QTAM_VS(1200, 0, 6, 10, 12, 10),
+    QTAM_VS(600, 1, 8, 25, 24),
     QTAM_VS(600, 2, 4, 25, 24),
     QTAM_VS(600, 2, 3, 24, 25),
+    QTAM_VS(300, 1, 12, 15, 20),
     QTAM_VS(300, 2, 4, 15, 20),
     QTAM_VS(300, 3, 2, 15, 20),
-    QTAM_VS(150, 4, 2, 10, 15),
     QTAM_VS(150, 3, 4, 10, 15),
+    QTAM_VS(150, 4, 2, 10, 15),
     QTAM_VN(75, 4, 3, 5, 15),
     QTAM_VS(8192, 0, 2, 16, 8, 8, 8),
     QTAM_VN(8192, 0, 2, 16, 16, 8, 4),

@@ -260,8 +260,8 @@ def test_tuned_defaults_per_length():
     plan of the same length keeps the first table-capable variant; M = 4800
     keeps its first registered one."""
     want = {32: "2400:16, 10, 15 rows/blk 2^0 minblk 6 threads 160",
-            16: "1200:10, 12, 10 rows/blk 2^0 minblk 8", 8: "600:25, 24 rows/blk 2^2 minblk 4",
-            4: "300:15, 20 rows/blk 2^2 minblk 4", 2: "150:10, 15 rows/blk 2^4 minblk 2"}
+            16: "1200:10, 12, 10 rows/blk 2^0 minblk 8", 8: "600:25, 24 rows/blk 2^1 minblk 8",
+            4: "300:15, 20 rows/blk 2^1 minblk 12", 2: "150:10, 15 rows/blk 2^3 minblk 4"}
     for dur, name in want.items():
         p = qtam.Plan(4096.0, 4096 * dur, (8.0, 16.0, 32.0), 20.0, 2048.0, 128, device=-1)
         assert qtam.qtam_variant_describe(p.info["row_variant"])["name"] == name
